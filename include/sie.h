@@ -1,0 +1,181 @@
+/*
+ * sie.h -- C ABI of the GB300 (sm_103a) AIM-accelerated surface-integral-
+ * equation library.
+ *
+ * The library implements the matrix-vector products and the solve of
+ * Sharma & Triverio, "An Accelerated Surface Integral Equation Method for the
+ * Electromagnetic Modeling of Dielectric and Lossy Objects of Arbitrary
+ * Conductivity":
+ *   - the RWG/Galerkin operators L and K of Eqs. (opL), (opK) for a medium
+ *     with complex wavenumber k (Eq. kin), Green's function of Eq. (Grrpki);
+ *   - their AIM form, Eqs. (AIM_Lin), (AIM_Kin): projection onto a uniform
+ *     grid, 3D FFT convolution with the sampled Green's function and its
+ *     gradient, interpolation back to the mesh, plus the precorrected sparse
+ *     near-region matrices of Eqs. (LinNRP), (KinNRP);
+ *   - the near-region-only interior operators used when the skin depth is
+ *     small (Sec. III-C, the 5-skin-depth cutoff of Sec. V);
+ *   - the GIBC system of Eq. (GIBCsys) with the interior operator of
+ *     Eqs. (nest02), (nest2), solved by GMRES (Sec. V), plane-wave excitation
+ *     (Sec. II) and the monostatic / bistatic RCS (Sec. V-A).
+ *
+ * Conventions
+ *   - Time dependence exp(+j w t).  k = sqrt(w mu (w eps - j sigma)) with
+ *     Im k <= 0 (Eq. kin).
+ *   - Complex numbers are interleaved (re, im) doubles (numpy complex128,
+ *     torch.complex128); complex64 buffers are interleaved floats.
+ *   - Vectors with nrhs right-hand sides are stored rhs-major: element n of
+ *     right-hand side r is at index r * len + n.
+ *   - Unknowns are RWG edge coefficients, numbered in increasing
+ *     (lower vertex id, higher vertex id) order of the edge; T+ is the
+ *     triangle in which the edge runs from the lower to the higher vertex id
+ *     in counter-clockwise (outward-normal) order.
+ *
+ * Ownership: every *_create / *_build call copies its host inputs; handles
+ * are opaque and must be destroyed in reverse order of creation (op, mesh,
+ * ctx).  Vector arguments are borrowed: with SIE_DEVICE_PTRS they are device
+ * pointers on the context's device, otherwise host pointers.
+ *
+ * Errors: every call returns a sie_status; nothing aborts or exits.
+ * sie_last_error() returns a message for the last failing call on the
+ * calling thread.  Calls on one context must not overlap in time (one host
+ * thread at a time); all device work is issued on the context's stream.
+ */
+#ifndef SIE_H
+#define SIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIE_OK = 0,
+    SIE_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, bad enum) */
+    SIE_ERR_MESH = 2,           /* mesh not a closed oriented 2-manifold, degenerate triangle */
+    SIE_ERR_OOM = 3,            /* device allocation failed */
+    SIE_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+    SIE_ERR_NOT_CONVERGED = 5,  /* GMRES reached maxit; x holds the last iterate */
+    SIE_ERR_TIMEOUT = 6,        /* a device-side wait gave up */
+    SIE_ERR_STATE = 7,          /* call not valid for this handle's state */
+    SIE_ERR_UNSUPPORTED = 8     /* valid request this build does not handle */
+} sie_status;
+
+typedef struct sie_ctx sie_ctx;
+typedef struct sie_mesh sie_mesh;
+typedef struct sie_op sie_op;
+
+enum { SIE_FP64 = 0, SIE_MIXED = 1 };          /* grid-path precision */
+enum { SIE_DEVICE_PTRS = 1 };                  /* flags: vector args are device pointers */
+
+/* Which operator sie_matvec applies. */
+enum {
+    SIE_OP_L0 = 0,  /* exterior L (background medium), AIM form           */
+    SIE_OP_K0 = 1,  /* exterior K (background medium), AIM form           */
+    SIE_OP_LI = 2,  /* interior L of the object (AIM or near-only)        */
+    SIE_OP_KI = 3,  /* interior K of the object (AIM or near-only)        */
+    SIE_OP_SYS = 4, /* GIBC system of Eq. (GIBCsys), divided by eta0      */
+    SIE_OP_ZI = 5   /* interior impedance Z_i of Eq. (GIBCdef) / eta0     */
+};
+
+/* Method parameters.  sie_params_default() fills the paper's values
+ * (Sec. IV-V) and the library's near-field quadrature defaults. */
+typedef struct {
+    double h;             /* grid spacing in metres; 0 = derive (below)                */
+    double h_over_edge;   /* h = h_over_edge * mean edge length (default 0.5) ...      */
+    int grid_n;           /* ... unless grid_n > 0: largest dimension has grid_n nodes */
+    int stencil_order;    /* M, Lagrange order per axis (default 2, Sec. IV)           */
+    int near_radius;      /* R_near in grid nodes (default 5: 11-node diameter, Sec. IV) */
+    double skin_cutoff;   /* interior pairs farther than this many skin depths dropped (5, Sec. V) */
+    int precision;        /* SIE_FP64 or SIE_MIXED (complex64 grid path)               */
+    double tol_outer;     /* GMRES relative residual, outer system (1e-4, Sec. V)      */
+    double tol_inner;     /* GMRES relative residual, nested interior system (1e-6)    */
+    int maxit;            /* outer iteration cap (800, Sec. V-A)                       */
+    int restart;          /* GMRES restart length (100)                                */
+    int inner_maxit;      /* nested iteration cap (200)                                */
+    /* near-field quadrature (the method's direct-integration rule) */
+    int q_far;            /* far-near pairs: q_far x q_far collapsed Gauss per triangle (5) */
+    int q_out;            /* close pairs: q_out x q_out outer points (5)                */
+    int q_ang;            /* polar inner rule: Gauss points per angular panel (8)       */
+    int q_rad;            /* polar inner rule: Gauss points per radial panel (8)        */
+    int q_npan;           /* radial panels graded toward the centre (5)                 */
+    int q_opan;           /* touching pairs: outer panels graded toward the feature (7) */
+    int q_olam;           /* touching pairs: points per graded outer panel (5)          */
+    int q_omu;            /* touching pairs: points across, vertex shared (6)           */
+    int q_emupan;         /* touching pairs: graded panels per half of a shared edge (2)*/
+    int q_emu;            /* touching pairs: points per shared-edge panel (4)           */
+    double q_ratio;       /* radial panel ratio (0.25)                                  */
+    double q_cf;          /* close if centroid distance < q_cf (R_t + R_s) (2.0)        */
+    double q_kres;        /* close if |k| (R_t + R_s) > q_kres (1.0)                    */
+    double q_alen;        /* longest angular (asinh) panel (1.5)                        */
+    double q_oratio;      /* outer panel ratio (0.25)                                   */
+} sie_params;
+
+void sie_params_default(sie_params* p);
+
+/* Context on one CUDA device.  stream: a cudaStream_t to issue work on, or
+ * NULL for a stream the context creates and owns. */
+sie_status sie_ctx_create(int device, void* stream, sie_ctx** out);
+sie_status sie_ctx_destroy(sie_ctx* ctx);
+const char* sie_last_error(void);
+
+/* Mesh: xyz (nv x 3, metres), tri (nt x 3, 0-based, counter-clockwise seen
+ * from outside).  Fails with SIE_ERR_MESH unless every edge is shared by
+ * exactly two oppositely oriented triangles.  One homogeneous object. */
+sie_status sie_mesh_create(sie_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                           sie_mesh** out);
+sie_status sie_mesh_destroy(sie_mesh* mesh);
+/* counts: out[0] = RWG edges N_e, out[1] = triangles N_t, out[2] = vertices */
+sie_status sie_mesh_counts(const sie_mesh* mesh, int64_t out[3]);
+
+/* Build the operators of one frequency.  Background medium: vacuum.  Object:
+ * (eps_r, mu_r, sigma).  Builds the exterior AIM operator (k0) and the
+ * interior operator (k_i): an AIM grid operator, or the near-region-only
+ * operator when 5 skin depths fit inside the near region (every kept pair is
+ * near; Sec. III-C).  Device memory is allocated here and freed by
+ * sie_op_destroy. */
+sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_r, double sigma,
+                        const sie_params* params, sie_op** out);
+sie_status sie_op_destroy(sie_op* op);
+
+/* Operator facts.  info (12 doubles): [0..2] grid N_x, N_y, N_z; [3..5] FFT
+ * n_x, n_y, n_z; [6] h; [7] near pairs (exterior); [8] nnz of the exterior
+ * near matrix; [9] interior mode (0 = AIM, 1 = near only); [10] interior near
+ * pairs; [11] grid origin x (origin y, z: see sie_op_grid). */
+sie_status sie_op_info(const sie_op* op, double info[12]);
+/* grid origin (3) and spacing of the exterior grid */
+sie_status sie_op_grid(const sie_op* op, double origin[3], double* h, int64_t N[3]);
+
+/* y = A x for nrhs right-hand sides, A selected by `which` (SIE_OP_*).
+ * x, y: complex128, length N_e (SYS: N_e as well: the AEFIE charge rows are
+ * eliminated, see sie_solve).  flags: SIE_DEVICE_PTRS or 0. */
+sie_status sie_matvec(sie_op* op, int which, const double* x, double* y, int nrhs, int flags);
+
+/* Export the precorrected near-region matrix of an operator
+ * (SIE_OP_L0/K0/LI/KI) as CSR on the host: call once with col/val NULL to get
+ * nnz in *nnz and row_ptr (N_e + 1) filled; then again with buffers of nnz
+ * entries.  val is complex128. */
+sie_status sie_op_near_csr(const sie_op* op, int which, int64_t* row_ptr, int32_t* col, double* val,
+                           int64_t* nnz);
+
+/* Right-hand side of Eq. (EFIE01dis) divided by eta0 for plane waves
+ * E_inc = epol exp(-j k0 khat . r) (khat unit propagation direction, epol
+ * orthogonal to it, |epol| = 1 V/m): b_m = -(1/eta0) I f_m . E_inc dS.
+ * khat, epol: nrhs x 3 doubles (host).  b: complex128 nrhs x N_e. */
+sie_status sie_rhs_planewave(sie_op* op, const double* khat, const double* epol, int nrhs, double* b, int flags);
+
+/* Solve SYS x = b by restarted GMRES (FP64 Arnoldi).  x: complex128 N_e x
+ * nrhs, H coefficients (n x H tested with RWG).  iters / relres: per rhs
+ * (host arrays of nrhs, may be NULL). */
+sie_status sie_solve(sie_op* op, const double* b, double* x, int nrhs, int* iters, double* relres, int flags);
+
+/* Monostatic/bistatic RCS (m^2) of the solution x (as returned by sie_solve,
+ * for the plane wave with polarisation epol, 1 V/m): for each observation
+ * direction rhat (ndir x 3, host) the far-field cross section
+ * 4 pi |E_s|^2 r^2.  rcs: ndir doubles (host).  One right-hand side. */
+sie_status sie_rcs(sie_op* op, const double* x, const double* rhat, int ndir, double* rcs, int flags);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIE_H */

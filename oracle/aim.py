@@ -310,24 +310,7 @@ class AIM:
         return L, K, LA, Lphi
 
     def exact_local(self, t, s, quad=None):
-        """Direct-integration 3x3 entries of pairs (t[i], s[i]) from the oracle moments."""
-        m = self.mesh
-        Mo = mom.pair_moments(m, np.stack([t, s], 1), self.k, quad)
-        ct = m.centroid[t]
-        cm, cn = self.coef[t], self.coef[s]
-        pm = m.V[m.tri_free[t]] - ct[:, None, :]
-        pn = m.V[m.tri_free[s]] - ct[:, None, :]
-        Q0, Q1, Q2, Q3, U, Vv = Mo[:, 0], Mo[:, 1:4], Mo[:, 4:7], Mo[:, 7], Mo[:, 8:11], Mo[:, 11:14]
-        LA = Q3[:, None, None] - np.einsum("pja,pa->pj", pn, Q1)[:, None, :] - np.einsum("pia,pa->pi", pm, Q2)[:, :, None] \
-            + np.einsum("pia,pja->pij", pm, pn) * Q0[:, None, None]
-        cc = cm[:, :, None] * cn[:, None, :]
-        LA = cc * LA
-        L = LA - 4.0 * cc * Q0[:, None, None] / self.k ** 2
-        dl = pn[:, None, :, :] - pm[:, :, None, :]
-        cx = np.cross(pn[:, None, :, :], pm[:, :, None, :])
-        K = cc * (np.einsum("pija,pa->pij", dl, U) + np.einsum("pija,pa->pij", cx, Vv))
-        Lphi = Q0 / (m.area[t] * m.area[s])
-        return L, K, LA, Lphi
+        return exact_local(self.mesh, self.k, t, s, quad)
 
     def build_near(self, quad=None, chunk=256):
         m = self.mesh
@@ -356,6 +339,74 @@ class AIM:
 
     def K(self, x):
         return self.NK @ x + self.grid_K(x)
+
+
+def exact_local(m, k, t, s, quad=None):
+    """Direct-integration 3x3 entries of pairs (t[i], s[i]) from the oracle moments:
+    returns L, K, LA (np, 3, 3) and Lphi (np,)."""
+    k = complex(k)
+    Mo = mom.pair_moments(m, np.stack([t, s], 1), k, quad)
+    coef = m.coef()
+    ct = m.centroid[t]
+    cm, cn = coef[t], coef[s]
+    pm = m.V[m.tri_free[t]] - ct[:, None, :]
+    pn = m.V[m.tri_free[s]] - ct[:, None, :]
+    Q0, Q1, Q2, Q3, U, Vv = Mo[:, 0], Mo[:, 1:4], Mo[:, 4:7], Mo[:, 7], Mo[:, 8:11], Mo[:, 11:14]
+    LA = Q3[:, None, None] - np.einsum("pja,pa->pj", pn, Q1)[:, None, :] - np.einsum("pia,pa->pi", pm, Q2)[:, :, None] \
+        + np.einsum("pia,pja->pij", pm, pn) * Q0[:, None, None]
+    cc = cm[:, :, None] * cn[:, None, :]
+    LA = cc * LA
+    L = LA - 4.0 * cc * Q0[:, None, None] / k ** 2
+    dl = pn[:, None, :, :] - pm[:, :, None, :]
+    cx = np.cross(pn[:, None, :, :], pm[:, :, None, :])
+    K = cc * (np.einsum("pija,pa->pij", dl, U) + np.einsum("pija,pa->pij", cx, Vv))
+    Lphi = Q0 / (m.area[t] * m.area[s])
+    return L, K, LA, Lphi
+
+
+def near_pairs_cutoff(m, cutoff):
+    """Interior skin-depth rule (Sec. V): keep the ordered pair (t, s) iff the
+    triangles touch or the gap |c_t - c_s| - R_t - R_s is <= cutoff (R = farthest
+    vertex from the centroid).  Sorted by (t, s).  Brute force (small meshes)."""
+    c = m.centroid
+    R = np.linalg.norm(m.V[m.T] - c[:, None, :], axis=2).max(1)
+    out = []
+    Tset = [set(tt) for tt in m.T.tolist()]
+    for t in range(m.nt):
+        gap = np.sqrt(((c - c[t]) ** 2).sum(1)) - R - R[t]
+        cand = np.nonzero(gap <= cutoff)[0].tolist()
+        touch = [s for s in range(m.nt) if Tset[t] & Tset[s]]
+        for s in sorted(set(cand) | set(touch)):
+            out.append((t, s))
+    return np.array(out, dtype=np.int64).reshape(-1, 2)
+
+
+class NearOnly:
+    """Interior operator when every pair kept by the skin-depth cutoff is a
+    near pair (Sec. III-C): L = L_NR, K = K_NR, no grid."""
+
+    def __init__(self, mesh, k, cutoff, quad=None, chunk=256):
+        self.mesh, self.k = mesh, complex(k)
+        self.pairs = near_pairs_cutoff(mesh, cutoff)
+        t, s = self.pairs[:, 0], self.pairs[:, 1]
+        rows, cols, vL, vK = [], [], [], []
+        for i0 in range(0, len(t), chunk):
+            tt, ss = t[i0:i0 + chunk], s[i0:i0 + chunk]
+            L, K, _, _ = exact_local(mesh, self.k, tt, ss, quad)
+            vL.append(L.ravel())
+            vK.append(K.ravel())
+            rows.append(np.repeat(mesh.tri_edge[tt], 3, axis=1).ravel())
+            cols.append(np.tile(mesh.tri_edge[ss], (1, 3)).ravel())
+        r, c = np.concatenate(rows), np.concatenate(cols)
+        sh = (mesh.ne, mesh.ne)
+        self.NL = sp.coo_matrix((np.concatenate(vL), (r, c)), shape=sh).tocsr()
+        self.NK = sp.coo_matrix((np.concatenate(vK), (r, c)), shape=sh).tocsr()
+
+    def L(self, x):
+        return self.NL @ x
+
+    def K(self, x):
+        return self.NK @ x
 
 
 def near_pairs(aim, g):

@@ -1,0 +1,193 @@
+"""Python binding of the sm_103a AIM surface-integral-equation library.
+
+Thin ctypes marshalling over the C ABI declared in ``include/sie.h``: every
+step of the computation runs in the library's CUDA kernels.  The binding
+fails loudly (``ImportError`` on first use) when ``_libsie.so`` is missing;
+there is no CPU fallback.
+
+Vectors may be numpy arrays (host; complex128) or CUDA torch tensors
+(complex128, contiguous) -- the latter are passed as device pointers.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_libsie.so")
+_lib = None
+
+SIE_OK = 0
+SIE_ERR_NOT_CONVERGED = 5
+SIE_FP64, SIE_MIXED = 0, 1
+SIE_DEVICE_PTRS = 1
+SIE_OP_L0, SIE_OP_K0, SIE_OP_LI, SIE_OP_KI, SIE_OP_SYS, SIE_OP_ZI = range(6)
+
+_STATUS = {0: "SIE_OK", 1: "SIE_ERR_ARG", 2: "SIE_ERR_MESH", 3: "SIE_ERR_OOM", 4: "SIE_ERR_CUDA",
+           5: "SIE_ERR_NOT_CONVERGED", 6: "SIE_ERR_TIMEOUT", 7: "SIE_ERR_STATE", 8: "SIE_ERR_UNSUPPORTED"}
+
+# every symbol the header declares
+SYMBOLS = ["sie_params_default", "sie_ctx_create", "sie_ctx_destroy", "sie_last_error", "sie_mesh_create",
+           "sie_mesh_destroy", "sie_mesh_counts", "sie_op_build", "sie_op_destroy", "sie_op_info", "sie_op_grid",
+           "sie_matvec", "sie_op_near_csr", "sie_rhs_planewave", "sie_solve", "sie_rcs"]
+
+
+class sie_params(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("h_over_edge", ctypes.c_double), ("grid_n", ctypes.c_int),
+                ("stencil_order", ctypes.c_int), ("near_radius", ctypes.c_int), ("skin_cutoff", ctypes.c_double),
+                ("precision", ctypes.c_int), ("tol_outer", ctypes.c_double), ("tol_inner", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("inner_maxit", ctypes.c_int),
+                ("q_far", ctypes.c_int), ("q_out", ctypes.c_int), ("q_ang", ctypes.c_int), ("q_rad", ctypes.c_int),
+                ("q_npan", ctypes.c_int), ("q_opan", ctypes.c_int), ("q_olam", ctypes.c_int),
+                ("q_omu", ctypes.c_int), ("q_emupan", ctypes.c_int), ("q_emu", ctypes.c_int),
+                ("q_ratio", ctypes.c_double), ("q_cf", ctypes.c_double), ("q_kres", ctypes.c_double),
+                ("q_alen", ctypes.c_double), ("q_oratio", ctypes.c_double)]
+
+
+class SieError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load ``_libsie.so`` (built by ``build.build()`` or ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_SO):
+            raise ImportError(f"{_SO} is missing: build it with paper_2003_11679_gb300.build.build()")
+        L = ctypes.CDLL(_SO)
+        P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        L.sie_params_default.argtypes = [ctypes.POINTER(sie_params)]
+        L.sie_params_default.restype = None
+        L.sie_last_error.restype = ctypes.c_char_p
+        L.sie_ctx_create.argtypes = [I, P, PP]
+        L.sie_ctx_destroy.argtypes = [P]
+        L.sie_mesh_create.argtypes = [P, P, I64, P, I64, PP]
+        L.sie_mesh_destroy.argtypes = [P]
+        L.sie_mesh_counts.argtypes = [P, P]
+        L.sie_op_build.argtypes = [P, D, D, D, D, ctypes.POINTER(sie_params), PP]
+        L.sie_op_destroy.argtypes = [P]
+        L.sie_op_info.argtypes = [P, P]
+        L.sie_op_grid.argtypes = [P, P, P, P]
+        L.sie_matvec.argtypes = [P, I, P, P, I, I]
+        L.sie_op_near_csr.argtypes = [P, I, P, P, P, P]
+        L.sie_rhs_planewave.argtypes = [P, P, P, I, P, I]
+        L.sie_solve.argtypes = [P, P, P, I, P, P, I]
+        L.sie_rcs.argtypes = [P, P, P, I, P, I]
+        for name in SYMBOLS:
+            f = getattr(L, name)
+            if name not in ("sie_params_default", "sie_last_error"):
+                f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != SIE_OK:
+        raise SieError(code, lib().sie_last_error().decode())
+
+
+def params(**kw):
+    p = sie_params()
+    lib().sie_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), a.is_cuda
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data), False
+
+
+class Context:
+    def __init__(self, device=0, stream=None):
+        self.h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream) if stream is not None else None
+        _check(lib().sie_ctx_create(device, s, ctypes.byref(self.h)))
+
+    def close(self):
+        if self.h:
+            _check(lib().sie_ctx_destroy(self.h))
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    def __init__(self, ctx, verts, tris):
+        self.ctx = ctx
+        V = np.ascontiguousarray(verts, dtype=np.float64)
+        T = np.ascontiguousarray(tris, dtype=np.int32)
+        self.h = ctypes.c_void_p()
+        _check(lib().sie_mesh_create(ctx.h, V.ctypes.data, len(V), T.ctypes.data, len(T), ctypes.byref(self.h)))
+        c = np.zeros(3, np.int64)
+        _check(lib().sie_mesh_counts(self.h, c.ctypes.data))
+        self.ne, self.nt, self.nv = int(c[0]), int(c[1]), int(c[2])
+
+    def close(self):
+        if self.h:
+            _check(lib().sie_mesh_destroy(self.h))
+            self.h = ctypes.c_void_p()
+
+
+class Operator:
+    """Operators of one frequency: exterior AIM (vacuum) and interior (object)."""
+
+    def __init__(self, mesh, freq, eps_r=1.0, mu_r=1.0, sigma=0.0, prm=None):
+        self.mesh = mesh
+        self.h = ctypes.c_void_p()
+        p = prm if prm is not None else params()
+        _check(lib().sie_op_build(mesh.h, freq, eps_r, mu_r, sigma, ctypes.byref(p), ctypes.byref(self.h)))
+
+    def info(self):
+        a = np.zeros(12)
+        _check(lib().sie_op_info(self.h, a.ctypes.data))
+        return a
+
+    def grid(self):
+        o = np.zeros(3)
+        h = ctypes.c_double()
+        N = np.zeros(3, np.int64)
+        _check(lib().sie_op_grid(self.h, o.ctypes.data, ctypes.byref(h), N.ctypes.data))
+        return o, h.value, N
+
+    def matvec(self, which, x, y=None, nrhs=1):
+        """y = A x; x numpy (host) or CUDA tensor (device), complex128."""
+        if y is None:
+            y = np.zeros_like(x)
+        px, dx = _ptr(x)
+        py, dy = _ptr(y)
+        if dx != dy:
+            raise ValueError("x and y must both be host or both be device buffers")
+        _check(lib().sie_matvec(self.h, which, px, py, nrhs, SIE_DEVICE_PTRS if dx else 0))
+        return y
+
+    def near_csr(self, which):
+        rp = np.zeros(self.mesh.ne + 1, np.int64)
+        nnz = ctypes.c_int64()
+        _check(lib().sie_op_near_csr(self.h, which, rp.ctypes.data, None, None, ctypes.byref(nnz)))
+        col = np.zeros(nnz.value, np.int32)
+        val = np.zeros(nnz.value, np.complex128)
+        _check(lib().sie_op_near_csr(self.h, which, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                     ctypes.byref(nnz)))
+        return rp, col, val
+
+    def close(self):
+        if self.h:
+            _check(lib().sie_op_destroy(self.h))
+            self.h = ctypes.c_void_p()

@@ -1,0 +1,732 @@
+// AIM grid path of Eqs. (AIM_Lin), (AIM_Kin) on sm_103a:
+//   projection P / P_phi (moment-matching stencils, scatter),
+//   zero-padded 3D FFT (shared-memory radix-2 pencils, pruned passes),
+//   spectral multiply with the sampled Green's function and its gradient,
+//   pruned inverse FFT, interpolation W = P^T (gather), and the
+//   precorrected near-region CSR product (Eqs. LinNRP, KinNRP).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+namespace sie {
+
+// ------------------------------------------------------------------ device mesh
+template <class T>
+static sie_status up(cudaStream_t st, T** d, const T* h, size_t n)
+{
+    SIE_CUDA_TRY(cudaMallocAsync((void**)d, sizeof(T) * std::max<size_t>(n, 1), st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(*d, h, sizeof(T) * n, cudaMemcpyHostToDevice, st));
+    return SIE_OK;
+}
+
+sie_status dev_upload_mesh(sie_mesh* m)
+{
+    cudaStream_t st = m->ctx->stream;
+    const HostMesh& h = m->h;
+    DevMesh& d = m->d;
+    d.nt = (int)h.nt;
+    d.ne = (int)h.ne;
+    d.nv = (int)h.nv;
+    SIE_TRY(up(st, &d.V, h.V.data(), h.V.size()));
+    SIE_TRY(up(st, &d.T, h.T.data(), h.T.size()));
+    SIE_TRY(up(st, &d.tri_edge, h.tri_edge.data(), h.tri_edge.size()));
+    SIE_TRY(up(st, &d.coef, h.coef.data(), h.coef.size()));
+    SIE_TRY(up(st, &d.q, h.q.data(), h.q.size()));
+    SIE_TRY(up(st, &d.cen, h.cen.data(), h.cen.size()));
+    SIE_TRY(up(st, &d.area, h.area.data(), h.area.size()));
+    SIE_TRY(up(st, &d.rad, h.rad.data(), h.rad.size()));
+    SIE_TRY(up(st, &d.edge_tri, h.edge_tri.data(), h.edge_tri.size()));
+    SIE_TRY(up(st, &d.edge_slot, h.edge_slot.data(), h.edge_slot.size()));
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIE_OK;
+}
+
+sie_status dev_free_mesh(sie_mesh* m)
+{
+    DevMesh& d = m->d;
+    void* ptrs[] = {d.V, d.T, d.tri_edge, d.coef, d.q, d.cen, d.area, d.rad, d.edge_tri, d.edge_slot};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    d = DevMesh();
+    return SIE_OK;
+}
+
+// ------------------------------------------------------------------ weights (moment matching)
+__constant__ double c_glx[16], c_glw[16];
+
+// w[t][u] = (I_t l_u, I_t (r - c_t) l_u): tensor Lagrange basis of order M on the
+// stencil nodes base + {0..M}^3, collapsed Gauss rule with p points per direction.
+__global__ void k_weights(int nt, int Mord, int p, DevMesh M, const int32_t* __restrict__ base, double ox, double oy,
+                          double oz, double h, double* __restrict__ W)
+{
+    const int Mp = Mord + 1, S = Mp * Mp * Mp;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nt * S) return;
+    int t = idx / S, u = idx % S;
+    int ux = u % Mp, uy = (u / Mp) % Mp, uz = u / (Mp * Mp);
+    const double* a = M.V + 3 * M.T[3 * t];
+    const double* b = M.V + 3 * M.T[3 * t + 1];
+    const double* c = M.V + 3 * M.T[3 * t + 2];
+    double e1[3], e2[3];
+    for (int d = 0; d < 3; d++) {
+        e1[d] = b[d] - a[d];
+        e2[d] = c[d] - a[d];
+    }
+    double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2], nz = e1[0] * e2[1] - e1[1] * e2[0];
+    double twoA = sqrt(nx * nx + ny * ny + nz * nz);
+    const double o[3] = {ox, oy, oz};
+    const int uu[3] = {ux, uy, uz};
+    double w0 = 0, w1[3] = {0, 0, 0};
+    for (int i = 0; i < p; i++) {
+        double uq = c_glx[i];
+        for (int j = 0; j < p; j++) {
+            double vq = c_glx[j] * (1.0 - uq);
+            double wq = twoA * (1.0 - uq) * c_glw[i] * c_glw[j];
+            double r[3], l = 1.0;
+            for (int d = 0; d < 3; d++) {
+                r[d] = a[d] + uq * e1[d] + vq * e2[d];
+                double xi = (r[d] - o[d]) / h - base[3 * t + d];
+                for (int m = 0; m < Mp; m++)
+                    if (m != uu[d]) l *= (xi - m) / (double)(uu[d] - m);
+            }
+            w0 += wq * l;
+            for (int d = 0; d < 3; d++) w1[d] += wq * (r[d] - M.cen[3 * t + d]) * l;
+        }
+    }
+    double* o4 = W + (size_t)idx * 4;
+    o4[0] = w0;
+    o4[1] = w1[0];
+    o4[2] = w1[1];
+    o4[3] = w1[2];
+}
+
+sie_status aim_weights(sie_op* op)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const GridDesc& g = op->ext.g;
+    int p = (3 * g.M + 4) / 2;  // ceil((3M+3)/2): exact to degree 3M+1
+    double x[16], w[16];
+    gauss_legendre01(p, x, w);
+    SIE_CUDA_TRY(cudaMemcpyToSymbolAsync(c_glx, x, sizeof(double) * p, 0, cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaMemcpyToSymbolAsync(c_glw, w, sizeof(double) * p, 0, cudaMemcpyHostToDevice, st));
+    int S = (g.M + 1) * (g.M + 1) * (g.M + 1);
+    int nt = op->mesh->d.nt;
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->W, sizeof(double) * 4 * (size_t)nt * S, st));
+    k_weights<<<(nt * S + 127) / 128, 128, 0, st>>>(nt, g.M, p, op->mesh->d, op->base, g.o[0], g.o[1], g.o[2], g.h,
+                                                    op->W);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+// ------------------------------------------------------------------ FFT
+// Twiddles exp(-2 pi i k / n), k < n/2, for n = 2^l (l <= 10), concatenated.
+static double2* g_tw[11] = {nullptr};
+static int g_tw_dev[11] = {-1};
+
+static sie_status twiddles(int logn, cudaStream_t st, double2** out)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_tw[logn] && g_tw_dev[logn] == dev) {
+        *out = g_tw[logn];
+        return SIE_OK;
+    }
+    int n = 1 << logn;
+    std::vector<double2> h(std::max(n / 2, 1));
+    for (int k = 0; k < n / 2; k++) {
+        long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)n;
+        h[k] = make_double2((double)cosl(a), (double)sinl(a));
+    }
+    double2* d = nullptr;
+    SIE_CUDA_TRY(cudaMalloc((void**)&d, sizeof(double2) * h.size()));
+    SIE_CUDA_TRY(cudaMemcpy(d, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice));
+    g_tw[logn] = d;
+    g_tw_dev[logn] = dev;
+    *out = d;
+    return SIE_OK;
+}
+
+struct PassGeom {
+    int n_in, n_out;       // elements read / written per pencil (zero padding / truncation)
+    int64_t npencil;       // pencils
+    int L;                 // pencil p -> lo = p % L, hi = p / L
+    int64_t slo_in, shi_in, st_in;
+    int64_t slo_out, shi_out, st_out;
+    int contig;            // 1: elements of a pencil are contiguous (x pass)
+};
+
+// One CTA transforms PB pencils of length n = 2^LOGN held in shared memory.
+// Load at bit-reversed positions, log2(n) radix-2 DIT stages, store.
+template <int LOGN, int PB>
+__global__ void __launch_bounds__(256) k_fft_pass(const double2* in, double2* out,  // may alias (in place)
+                                                  const double2* __restrict__ tw, int inv, PassGeom G)
+{
+    constexpr int n = 1 << LOGN;
+    constexpr int pitch = n + 1;
+    extern __shared__ double2 sm[];
+    const int64_t p0 = (int64_t)blockIdx.x * PB;
+    // load (zero padded)
+    for (int idx = threadIdx.x; idx < PB * n; idx += blockDim.x) {
+        int pl, j;
+        if (G.contig) {
+            pl = idx / n;
+            j = idx % n;
+        } else {
+            pl = idx % PB;
+            j = idx / PB;
+        }
+        int64_t p = p0 + pl;
+        double2 v = make_double2(0.0, 0.0);
+        if (p < G.npencil && j < G.n_in) {
+            int64_t b = (p % G.L) * G.slo_in + (p / G.L) * G.shi_in;
+            v = in[b + (int64_t)j * G.st_in];
+        }
+        sm[pl * pitch + (__brev(j) >> (32 - LOGN))] = v;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int s = 1; s <= LOGN; s++) {
+        const int half = 1 << (s - 1);
+        for (int bfly = threadIdx.x; bfly < PB * (n / 2); bfly += blockDim.x) {
+            int pl = bfly / (n / 2), bb = bfly % (n / 2);
+            int grp = bb >> (s - 1), pos = bb & (half - 1);
+            int i0 = grp * 2 * half + pos, i1 = i0 + half;
+            double2 w = tw[pos << (LOGN - s)];
+            if (inv) w.y = -w.y;
+            double2 u = sm[pl * pitch + i0], v = sm[pl * pitch + i1];
+            double2 vw = make_double2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+            sm[pl * pitch + i0] = make_double2(u.x + vw.x, u.y + vw.y);
+            sm[pl * pitch + i1] = make_double2(u.x - vw.x, u.y - vw.y);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < PB * n; idx += blockDim.x) {
+        int pl, j;
+        if (G.contig) {
+            pl = idx / n;
+            j = idx % n;
+        } else {
+            pl = idx % PB;
+            j = idx / PB;
+        }
+        int64_t p = p0 + pl;
+        if (p < G.npencil && j < G.n_out) {
+            int64_t b = (p % G.L) * G.slo_out + (p / G.L) * G.shi_out;
+            out[b + (int64_t)j * G.st_out] = sm[pl * pitch + j];
+        }
+    }
+}
+
+template <int LOGN>
+static sie_status launch_pass_n(cudaStream_t st, const double2* in, double2* out, int inv, const PassGeom& G)
+{
+    constexpr int n = 1 << LOGN;
+    constexpr int PB = (n >= 512) ? 8 : 16;
+    double2* tw = nullptr;
+    SIE_TRY(twiddles(LOGN, st, &tw));
+    size_t smem = sizeof(double2) * PB * (n + 1);
+    static bool attr = false;
+    if (!attr) {
+        SIE_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<LOGN, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    unsigned blocks = (unsigned)((G.npencil + PB - 1) / PB);
+    k_fft_pass<LOGN, PB><<<blocks, 256, smem, st>>>(in, out, tw, inv, G);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+static sie_status launch_pass(cudaStream_t st, int n, const double2* in, double2* out, int inv, const PassGeom& G)
+{
+    switch (n) {
+        case 16: return launch_pass_n<4>(st, in, out, inv, G);
+        case 32: return launch_pass_n<5>(st, in, out, inv, G);
+        case 64: return launch_pass_n<6>(st, in, out, inv, G);
+        case 128: return launch_pass_n<7>(st, in, out, inv, G);
+        case 256: return launch_pass_n<8>(st, in, out, inv, G);
+        case 512: return launch_pass_n<9>(st, in, out, inv, G);
+        case 1024: return launch_pass_n<10>(st, in, out, inv, G);
+    }
+    set_error("unsupported FFT length");
+    return SIE_ERR_UNSUPPORTED;
+}
+
+// dir = -1: forward transform of the compact N grid `src` (or, prune = 0, of the
+// full n grid already in buf) into the full spectrum in buf.
+// dir = +1: inverse of the spectrum in buf; prune = 1 writes only the physical
+// N box into the compact array `src` (used as output), prune = 0 keeps n^3 in buf.
+sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune)
+{
+    const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int64_t Nx = prune ? g.N[0] : nx, Ny = prune ? g.N[1] : ny, Nz = prune ? g.N[2] : nz;
+    const int64_t pyz = nx * ny;  // padded plane
+    if (dir < 0) {
+        // x pass: pencils (y < Ny, z < Nz)
+        PassGeom X{(int)Nx, (int)nx, Ny * Nz, (int)Ny, prune ? Nx : nx, prune ? Nx * Ny : pyz, 1, nx, pyz, 1, 1};
+        SIE_TRY(launch_pass(st, (int)nx, prune ? src : buf, buf, 0, X));
+        // y pass: pencils (x < nx, z < Nz)
+        PassGeom Y{(int)Ny, (int)ny, nx * Nz, (int)nx, 1, pyz, nx, 1, pyz, nx, 0};
+        SIE_TRY(launch_pass(st, (int)ny, buf, buf, 0, Y));
+        // z pass: pencils (x < nx, y < ny)
+        PassGeom Z{(int)Nz, (int)nz, nx * ny, (int)nx, 1, nx, pyz, 1, nx, pyz, 0};
+        SIE_TRY(launch_pass(st, (int)nz, buf, buf, 0, Z));
+    } else {
+        PassGeom Z{(int)nz, (int)Nz, nx * ny, (int)nx, 1, nx, pyz, 1, nx, pyz, 0};
+        SIE_TRY(launch_pass(st, (int)nz, buf, buf, 1, Z));
+        PassGeom Y{(int)ny, (int)Ny, nx * Nz, (int)nx, 1, pyz, nx, 1, pyz, nx, 0};
+        SIE_TRY(launch_pass(st, (int)ny, buf, buf, 1, Y));
+        double2* dst = prune ? const_cast<double2*>(src) : buf;
+        PassGeom X{(int)nx, (int)Nx, Ny * Nz, (int)Ny, nx, pyz, 1, prune ? Nx : nx, prune ? Nx * Ny : pyz, 1, 1};
+        SIE_TRY(launch_pass(st, (int)nx, buf, dst, 1, X));
+    }
+    return SIE_OK;
+}
+
+// ------------------------------------------------------------------ kernel spectra
+// circulant samples of G, dG/dx, dG/dy, dG/dz at lattice lags (c9 reading:
+// index i -> lag i if i < N, i - n if i > n - N, else unused); G(0) = 0.
+// Scaled by 1/(nx ny nz) so the unnormalised inverse FFT gives the convolution.
+__global__ void k_sample(GridDesc g, double kr, double ki, double2* __restrict__ spec, int64_t nn)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nn) return;
+    int ix = (int)(idx % g.n[0]), iy = (int)((idx / g.n[0]) % g.n[1]), iz = (int)(idx / ((int64_t)g.n[0] * g.n[1]));
+    int ii[3] = {ix, iy, iz};
+    double d[3];
+    bool ok = true;
+    for (int a = 0; a < 3; a++) {
+        int lag;
+        if (ii[a] < g.N[a])
+            lag = ii[a];
+        else if (ii[a] > g.n[a] - g.N[a])
+            lag = ii[a] - g.n[a];
+        else {
+            lag = 0;
+            ok = false;
+        }
+        d[a] = g.h * lag;
+    }
+    double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double2 G = make_double2(0, 0), gx = G, gy = G, gz = G;
+    if (ok && R > 0) {
+        double sc = 1.0 / ((double)g.n[0] * g.n[1] * g.n[2]);
+        double e = exp(ki * R), s, c;
+        sincos(-kr * R, &s, &c);
+        double er = e * c, ei = e * s;  // exp(-j k R)
+        G = make_double2(sc * er / (4 * M_PI * R), sc * ei / (4 * M_PI * R));
+        // g = -(1 + j k R) e / (4 pi R^3)
+        double ar = 1.0 - ki * R, ai = kr * R;
+        double fr = -(ar * er - ai * ei) / (4 * M_PI * R * R * R) * sc;
+        double fi = -(ar * ei + ai * er) / (4 * M_PI * R * R * R) * sc;
+        gx = make_double2(fr * d[0], fi * d[0]);
+        gy = make_double2(fr * d[1], fi * d[1]);
+        gz = make_double2(fr * d[2], fi * d[2]);
+    }
+    spec[idx] = G;
+    spec[nn + idx] = gx;
+    spec[2 * nn + idx] = gy;
+    spec[3 * nn + idx] = gz;
+}
+
+__global__ void k_to_c64(const double2* __restrict__ a, float2* __restrict__ b, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+sie_status aim_spectra(sie_op* op, AimOp& a)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const GridDesc& g = a.g;
+    int64_t nn = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&a.spec, sizeof(double2) * 4 * nn, st));
+    k_sample<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(g, a.kr, a.ki, a.spec, nn);
+    SIE_CUDA_TRY(cudaGetLastError());
+    for (int c = 0; c < 4; c++) SIE_TRY(fft3d(st, a.spec + c * nn, nullptr, g, -1, 0));
+    return SIE_OK;
+}
+
+// ------------------------------------------------------------------ projection (P, P_phi)
+// one thread per (triangle, stencil node): J_t(r) = alpha (r - c_t) + beta,
+// alpha = sum_i c_i x_i, beta = sum_i c_i x_i (c_t - p_i), div J_t = 2 alpha.
+// mode 0: grids Jx, Jy, Jz, rho; mode 1: Jx, Jy, Jz only.
+__global__ void k_project(int nt, int S, int Mord, DevMesh M, const int32_t* __restrict__ base,
+                          const double* __restrict__ W, const double2* __restrict__ x, GridDesc g, int ngrid,
+                          double2* __restrict__ src, int64_t Ng)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nt * S) return;
+    int t = idx / S, u = idx % S;
+    const int Mp = Mord + 1;
+    double2 al = make_double2(0, 0);
+    double2 be[3] = {al, al, al};
+    for (int i = 0; i < 3; i++) {
+        double2 xv = x[M.tri_edge[3 * t + i]];
+        double c = M.coef[3 * t + i];
+        al.x += c * xv.x;
+        al.y += c * xv.y;
+        for (int a = 0; a < 3; a++) {
+            double qq = c * M.q[9 * t + 3 * i + a];
+            be[a].x += qq * xv.x;
+            be[a].y += qq * xv.y;
+        }
+    }
+    int nx = base[3 * t] + u % Mp, ny = base[3 * t + 1] + (u / Mp) % Mp, nz = base[3 * t + 2] + u / (Mp * Mp);
+    int64_t node = ((int64_t)nz * g.N[1] + ny) * g.N[0] + nx;
+    const double* w = W + (size_t)idx * 4;
+    for (int a = 0; a < 3; a++) {
+        double2* d = src + a * Ng + node;
+        atomicAdd(&d->x, al.x * w[1 + a] + be[a].x * w[0]);
+        atomicAdd(&d->y, al.y * w[1 + a] + be[a].y * w[0]);
+    }
+    if (ngrid == 4) {
+        double2* d = src + 3 * Ng + node;
+        atomicAdd(&d->x, 2.0 * al.x * w[0]);
+        atomicAdd(&d->y, 2.0 * al.y * w[0]);
+    }
+}
+
+// ------------------------------------------------------------------ spectral multiply
+// mode 0 (L): J_a *= G, rho *= G.  mode 1 (K): J <- Ghat_grad x J.
+__global__ void k_specmul(int mode, const double2* __restrict__ spec, double2* __restrict__ buf, int64_t nn)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    auto mul = [](double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
+    if (mode == 0) {
+        double2 G = spec[i];
+        for (int c = 0; c < 4; c++) buf[c * nn + i] = mul(G, buf[c * nn + i]);
+    } else {
+        double2 gx = spec[nn + i], gy = spec[2 * nn + i], gz = spec[3 * nn + i];
+        double2 jx = buf[i], jy = buf[nn + i], jz = buf[2 * nn + i];
+        double2 a = mul(gy, jz), b = mul(gz, jy);
+        buf[i] = make_double2(a.x - b.x, a.y - b.y);
+        a = mul(gz, jx);
+        b = mul(gx, jz);
+        buf[nn + i] = make_double2(a.x - b.x, a.y - b.y);
+        a = mul(gx, jy);
+        b = mul(gy, jx);
+        buf[2 * nn + i] = make_double2(a.x - b.x, a.y - b.y);
+    }
+}
+
+// ------------------------------------------------------------------ interpolation (W = P^T)
+// one warp per triangle; lanes gather stencil nodes; y[e] += c_{t,i}
+// [S1 + (c_t - p_i) . T0 + scal 2 P0]  (scal = -1/k^2 for L, 0 for K)
+__global__ void k_interp(int nt, int S, int Mord, DevMesh M, const int32_t* __restrict__ base,
+                         const double* __restrict__ W, const double2* __restrict__ out, GridDesc g, int has_phi,
+                         double2 scal, int64_t Ng, double2* __restrict__ y)
+{
+    int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x & 31;
+    if (t >= nt) return;
+    const int Mp = Mord + 1;
+    double s1r = 0, s1i = 0, t0r[3] = {0, 0, 0}, t0i[3] = {0, 0, 0}, p0r = 0, p0i = 0;
+    for (int u = lane; u < S; u += 32) {
+        int nx = base[3 * t] + u % Mp, ny = base[3 * t + 1] + (u / Mp) % Mp, nz = base[3 * t + 2] + u / (Mp * Mp);
+        int64_t node = ((int64_t)nz * g.N[1] + ny) * g.N[0] + nx;
+        const double* w = W + ((size_t)t * S + u) * 4;
+        for (int a = 0; a < 3; a++) {
+            double2 A = out[a * Ng + node];
+            s1r += w[1 + a] * A.x;
+            s1i += w[1 + a] * A.y;
+            t0r[a] += w[0] * A.x;
+            t0i[a] += w[0] * A.y;
+        }
+        if (has_phi) {
+            double2 P = out[3 * Ng + node];
+            p0r += w[0] * P.x;
+            p0i += w[0] * P.y;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        s1r += __shfl_down_sync(0xffffffffu, s1r, off);
+        s1i += __shfl_down_sync(0xffffffffu, s1i, off);
+        p0r += __shfl_down_sync(0xffffffffu, p0r, off);
+        p0i += __shfl_down_sync(0xffffffffu, p0i, off);
+        for (int a = 0; a < 3; a++) {
+            t0r[a] += __shfl_down_sync(0xffffffffu, t0r[a], off);
+            t0i[a] += __shfl_down_sync(0xffffffffu, t0i[a], off);
+        }
+    }
+    if (lane < 3) {
+        int i = lane;
+        // broadcast from lane 0
+        double S1r = __shfl_sync(0x7u, s1r, 0), S1i = __shfl_sync(0x7u, s1i, 0);
+        double P0r = __shfl_sync(0x7u, p0r, 0), P0i = __shfl_sync(0x7u, p0i, 0);
+        double T0r[3], T0i[3];
+        for (int a = 0; a < 3; a++) {
+            T0r[a] = __shfl_sync(0x7u, t0r[a], 0);
+            T0i[a] = __shfl_sync(0x7u, t0i[a], 0);
+        }
+        double vr = S1r, vi = S1i;
+        for (int a = 0; a < 3; a++) {
+            double qq = M.q[9 * t + 3 * i + a];
+            vr += qq * T0r[a];
+            vi += qq * T0i[a];
+        }
+        if (has_phi) {
+            vr += 2.0 * (scal.x * P0r - scal.y * P0i);
+            vi += 2.0 * (scal.x * P0i + scal.y * P0r);
+        }
+        double c = M.coef[3 * t + i];
+        double2* d = y + M.tri_edge[3 * t + i];
+        atomicAdd(&d->x, c * vr);
+        atomicAdd(&d->y, c * vi);
+    }
+}
+
+// ------------------------------------------------------------------ near CSR product
+// y[m] += sum_e val[e] x[col[e]]; one warp per row
+__global__ void k_spmv(int nrow, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                       const double2* __restrict__ val, const double2* __restrict__ x, double2* __restrict__ y)
+{
+    int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x & 31;
+    if (r >= nrow) return;
+    double ar = 0, ai = 0;
+    for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += 32) {
+        double2 v = val[e], xv = x[col[e]];
+        ar += v.x * xv.x - v.y * xv.y;
+        ai += v.x * xv.y + v.y * xv.x;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        ar += __shfl_down_sync(0xffffffffu, ar, off);
+        ai += __shfl_down_sync(0xffffffffu, ai, off);
+    }
+    if (lane == 0) {
+        y[r].x += ar;
+        y[r].y += ai;
+    }
+}
+
+// y = A x for one right-hand side, A = L (which_LK = 0) or K (1) of operator a
+sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, double2* y)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const DevMesh& M = op->mesh->d;
+    SIE_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double2) * M.ne, st));
+    if (a.has_grid) {
+        const GridDesc& g = a.g;
+        int S = (g.M + 1) * (g.M + 1) * (g.M + 1);
+        int64_t Ng = (int64_t)g.N[0] * g.N[1] * g.N[2];
+        int64_t nn = (int64_t)g.n[0] * g.n[1] * g.n[2];
+        int ngrid = which_LK == 0 ? 4 : 3;
+        double2* src = op->ws.src;
+        double2* buf = op->ws.bufs;
+        SIE_CUDA_TRY(cudaMemsetAsync(src, 0, sizeof(double2) * ngrid * Ng, st));
+        k_project<<<(M.nt * S + 255) / 256, 256, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, x, g, ngrid, src, Ng);
+        SIE_CUDA_TRY(cudaGetLastError());
+        for (int c = 0; c < ngrid; c++) SIE_TRY(fft3d(st, buf + c * nn, src + c * Ng, g, -1, 1));
+        k_specmul<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(which_LK, a.spec, buf, nn);
+        SIE_CUDA_TRY(cudaGetLastError());
+        for (int c = 0; c < ngrid; c++) SIE_TRY(fft3d(st, buf + c * nn, src + c * Ng, g, +1, 1));
+        std::complex<double> kk(a.kr, a.ki);
+        std::complex<double> sc = -1.0 / (kk * kk);
+        k_interp<<<(M.nt + 3) / 4, 128, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, src, g, which_LK == 0,
+                                                 make_double2(sc.real(), sc.imag()), Ng, y);
+        SIE_CUDA_TRY(cudaGetLastError());
+    }
+    k_spmv<<<(M.ne + 3) / 4, 128, 0, st>>>(M.ne, a.row_ptr, a.col, which_LK == 0 ? a.valL : a.valK, x, y);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+static void free_aim(AimOp& a)
+{
+    void* ptrs[] = {a.spec, a.spec32, a.pairs, a.row_ptr, a.col, a.valL, a.valK};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    a.spec = nullptr;
+    a.spec32 = nullptr;
+    a.pairs = nullptr;
+    a.row_ptr = nullptr;
+    a.col = nullptr;
+    a.valL = a.valK = nullptr;
+}
+
+}  // namespace sie
+
+using namespace sie;
+
+extern "C" {
+
+sie_status sie_op_destroy(sie_op* op)
+{
+    if (!op) return SIE_ERR_ARG;
+    cudaSetDevice(op->mesh->ctx->device);
+    cudaStreamSynchronize(op->mesh->ctx->stream);
+    free_aim(op->ext);
+    free_aim(op->inn);
+    void* ptrs[] = {op->base, op->W, op->ws.bufs, op->ws.src, op->xtmp};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete op;
+    return SIE_OK;
+}
+
+sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_r, double sigma,
+                        const sie_params* params, sie_op** out)
+{
+    if (!mesh || !out || !(freq_hz > 0) || !(eps_r > 0) || !(mu_r > 0) || sigma < 0) {
+        set_error("sie_op_build: invalid argument");
+        return SIE_ERR_ARG;
+    }
+    SIE_CUDA_TRY(cudaSetDevice(mesh->ctx->device));
+    cudaStream_t st = mesh->ctx->stream;
+    auto* op = new sie_op();
+    op->mesh = mesh;
+    if (params)
+        op->p = *params;
+    else
+        sie_params_default(&op->p);
+    op->freq = freq_hz;
+    op->eps_r = eps_r;
+    op->mu_r = mu_r;
+    op->sigma = sigma;
+    const double c0 = 299792458.0, mu0 = 4e-7 * M_PI, eps0 = 1.0 / (mu0 * c0 * c0);
+    const double w = 2 * M_PI * freq_hz;
+    op->k0 = w / c0;
+    // Eq. (kin): k_i = sqrt(w mu (w eps - j sigma)), branch Im k <= 0
+    std::complex<double> ki = std::sqrt(std::complex<double>(w * mu0 * mu_r) * std::complex<double>(w * eps0 * eps_r, -sigma));
+    if (ki.imag() > 0) ki = -ki;
+    auto fail = [&](sie_status s) {
+        sie_op_destroy(op);
+        return s;
+    };
+    sie_status s;
+    // exterior grid (Sec. III-D: one global grid around the structure)
+    GridDesc g;
+    if ((s = make_grid(mesh->h, op->p, g)) != SIE_OK) return fail(s);
+    std::vector<int32_t> hb;
+    stencil_base(mesh->h, g, hb);
+    for (int64_t t = 0; t < mesh->h.nt; t++)
+        for (int d = 0; d < 3; d++)
+            if (hb[3 * t + d] < 0 || hb[3 * t + d] + g.M > g.N[d] - 1) {
+                set_error("stencil outside the grid");
+                return fail(SIE_ERR_MESH);
+            }
+    if ((s = up(st, &op->base, hb.data(), hb.size())) != SIE_OK) return fail(s);
+    op->ext.g = g;
+    op->ext.kr = op->k0;
+    op->ext.ki = 0.0;
+    op->ext.has_grid = true;
+    if ((s = aim_weights(op)) != SIE_OK) return fail(s);
+    QuadDev q;
+    make_quad(op->p, q);
+    if ((s = aim_spectra(op, op->ext)) != SIE_OK) return fail(s);
+    near_pairs_grid(mesh->h, g, hb, op->ext.hpairs);
+    if ((s = near_build(op, op->ext, q)) != SIE_OK) return fail(s);
+    // interior operator (Sec. III-C): near-only when every pair inside the
+    // skin-depth cutoff is a near pair, else AIM on the object grid (shared
+    // with the exterior grid for a single object)
+    op->inn.kr = ki.real();
+    op->inn.ki = ki.imag();
+    op->inn.g = g;
+    double delta = ki.imag() < 0 ? -1.0 / ki.imag() : 1e300;
+    double cut = op->p.skin_cutoff * delta;
+    if (cut <= (g.Rnear - g.M) * g.h) {
+        op->inn.has_grid = false;
+        near_pairs_cutoff(mesh->h, cut, op->inn.hpairs);
+    } else {
+        op->inn.has_grid = true;
+        if ((s = aim_spectra(op, op->inn)) != SIE_OK) return fail(s);
+        op->inn.hpairs = op->ext.hpairs;
+    }
+    if ((s = near_build(op, op->inn, q)) != SIE_OK) return fail(s);
+    // workspace
+    int64_t nn = (int64_t)g.n[0] * g.n[1] * g.n[2], Ng = (int64_t)g.N[0] * g.N[1] * g.N[2];
+    op->ws.grid_elems = nn;
+    cudaError_t e1 = cudaMallocAsync((void**)&op->ws.bufs, sizeof(double2) * 4 * nn, st);
+    cudaError_t e2 = cudaMallocAsync((void**)&op->ws.src, sizeof(double2) * 4 * Ng, st);
+    cudaError_t e3 = cudaMallocAsync((void**)&op->xtmp, sizeof(double2) * 4 * mesh->h.ne, st);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        set_error("sie_op_build: workspace allocation failed");
+        return fail(SIE_ERR_OOM);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_error(std::string("sie_op_build: ") + cudaGetErrorString(e));
+        return fail(SIE_ERR_CUDA);
+    }
+    *out = op;
+    return SIE_OK;
+}
+
+sie_status sie_matvec(sie_op* op, int which, const double* x, double* y, int nrhs, int flags)
+{
+    if (!op || !x || !y || nrhs < 1) {
+        set_error("sie_matvec: invalid argument");
+        return SIE_ERR_ARG;
+    }
+    if (which < SIE_OP_L0 || which > SIE_OP_KI) {
+        set_error("sie_matvec: operator not available in this build");
+        return SIE_ERR_UNSUPPORTED;
+    }
+    SIE_CUDA_TRY(cudaSetDevice(op->mesh->ctx->device));
+    cudaStream_t st = op->mesh->ctx->stream;
+    const int64_t ne = op->mesh->h.ne;
+    AimOp& a = (which == SIE_OP_L0 || which == SIE_OP_K0) ? op->ext : op->inn;
+    int lk = (which == SIE_OP_L0 || which == SIE_OP_LI) ? 0 : 1;
+    bool dev = flags & SIE_DEVICE_PTRS;
+    for (int r = 0; r < nrhs; r++) {
+        const double2* xr;
+        double2* yr;
+        if (dev) {
+            xr = (const double2*)x + r * ne;
+            yr = (double2*)y + r * ne;
+        } else {
+            SIE_CUDA_TRY(cudaMemcpyAsync(op->xtmp, (const double2*)x + r * ne, sizeof(double2) * ne,
+                                         cudaMemcpyHostToDevice, st));
+            xr = op->xtmp;
+            yr = op->xtmp + ne;
+        }
+        SIE_TRY(aim_apply(op, a, lk, xr, yr));
+        if (!dev)
+            SIE_CUDA_TRY(cudaMemcpyAsync((double2*)y + r * ne, yr, sizeof(double2) * ne, cudaMemcpyDeviceToHost, st));
+    }
+    if (!dev) SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIE_OK;
+}
+
+sie_status sie_op_near_csr(const sie_op* op, int which, int64_t* row_ptr, int32_t* col, double* val, int64_t* nnz)
+{
+    if (!op || !row_ptr || !nnz || which < SIE_OP_L0 || which > SIE_OP_KI) {
+        set_error("sie_op_near_csr: invalid argument");
+        return SIE_ERR_ARG;
+    }
+    const AimOp& a = (which == SIE_OP_L0 || which == SIE_OP_K0) ? op->ext : op->inn;
+    int lk = (which == SIE_OP_L0 || which == SIE_OP_LI) ? 0 : 1;
+    *nnz = a.nnz;
+    std::memcpy(row_ptr, a.csr.row_ptr.data(), sizeof(int64_t) * a.csr.row_ptr.size());
+    if (col) std::memcpy(col, a.csr.col.data(), sizeof(int32_t) * a.nnz);
+    if (val) {
+        SIE_CUDA_TRY(cudaSetDevice(op->mesh->ctx->device));
+        SIE_CUDA_TRY(cudaMemcpy(val, lk == 0 ? a.valL : a.valK, sizeof(double2) * a.nnz, cudaMemcpyDeviceToHost));
+    }
+    return SIE_OK;
+}
+
+sie_status sie_rhs_planewave(sie_op*, const double*, const double*, int, double*, int)
+{
+    set_error("sie_rhs_planewave: not available in this build");
+    return SIE_ERR_UNSUPPORTED;
+}
+
+sie_status sie_solve(sie_op*, const double*, double*, int, int*, double*, int)
+{
+    set_error("sie_solve: not available in this build");
+    return SIE_ERR_UNSUPPORTED;
+}
+
+sie_status sie_rcs(sie_op*, const double*, const double*, int, double*, int)
+{
+    set_error("sie_rcs: not available in this build");
+    return SIE_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

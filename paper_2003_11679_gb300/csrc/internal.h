@@ -1,0 +1,166 @@
+// Internal declarations of the sm_103a AIM/SIE library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sie.h"
+
+namespace sie {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+struct Status {
+    sie_status code = SIE_OK;
+};
+#define SIE_CUDA_TRY(call)                                                                       \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            ::sie::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+            return e_ == cudaErrorMemoryAllocation ? SIE_ERR_OOM : SIE_ERR_CUDA;                  \
+        }                                                                                         \
+    } while (0)
+#define SIE_TRY(call)                      \
+    do {                                   \
+        sie_status s_ = (call);            \
+        if (s_ != SIE_OK) return s_;       \
+    } while (0)
+
+// ------------------------------------------------------------------ geometry
+// Host-side mesh with its RWG table.  Slot i of triangle t is the edge
+// opposite local vertex i; sign +1 on T+, -1 on T-; the free vertex of slot i
+// is vertex i of the triangle.
+struct HostMesh {
+    int64_t nv = 0, nt = 0, ne = 0;
+    std::vector<double> V;           // nv*3
+    std::vector<int32_t> T;          // nt*3
+    std::vector<int32_t> tri_edge;   // nt*3
+    std::vector<int8_t> tri_sign;    // nt*3
+    std::vector<double> edge_len;    // ne
+    std::vector<int32_t> edge_tri;   // ne*2 (T+, T-)
+    std::vector<int8_t> edge_slot;   // ne*2 slot of the edge in T+, T-
+    std::vector<double> area;        // nt
+    std::vector<double> cen;         // nt*3
+    std::vector<double> nrm;         // nt*3 unit normal
+    std::vector<double> coef;        // nt*3 = s l / (2A)
+    std::vector<double> q;           // nt*9 = c_t - p (slot-major, then xyz)
+    std::vector<double> rad;         // nt farthest vertex from the centroid
+    double mean_edge = 0;
+};
+sie_status build_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, HostMesh& m);
+
+struct GridDesc {
+    double o[3];
+    double h;
+    int N[3];     // physical nodes per axis
+    int n[3];     // FFT lengths (powers of two >= 2N-1)
+    int M;        // Lagrange order
+    int Rnear;    // near radius (nodes)
+};
+sie_status make_grid(const HostMesh& m, const sie_params& p, GridDesc& g);
+void stencil_base(const HostMesh& m, const GridDesc& g, std::vector<int32_t>& base);
+
+// near triangle pairs, sorted by (t, s): AIM rule (Chebyshev distance of the
+// stencil centres <= Rnear) or interior cutoff rule (touching, or gap <= cutoff)
+void near_pairs_grid(const HostMesh& m, const GridDesc& g, const std::vector<int32_t>& base,
+                     std::vector<int32_t>& pairs);
+void near_pairs_cutoff(const HostMesh& m, double cutoff, std::vector<int32_t>& pairs);
+
+// CSR pattern over edges from a sorted triangle-pair list
+struct CsrPattern {
+    std::vector<int64_t> row_ptr;  // ne+1
+    std::vector<int32_t> col;      // nnz
+};
+void edge_csr_pattern(const HostMesh& m, const std::vector<int32_t>& pairs, CsrPattern& csr);
+
+// Gauss-Legendre on [0, 1] by Newton iteration on the Legendre recurrence
+void gauss_legendre01(int n, double* x, double* w);
+
+// ------------------------------------------------------------------ device data
+struct DevMesh {
+    int nt = 0, ne = 0, nv = 0;
+    double* V = nullptr;        // nv*3
+    int32_t* T = nullptr;       // nt*3
+    int32_t* tri_edge = nullptr;
+    double* coef = nullptr;     // nt*3
+    double* q = nullptr;        // nt*9
+    double* cen = nullptr;      // nt*3
+    double* area = nullptr;     // nt
+    double* rad = nullptr;      // nt
+    int32_t* edge_tri = nullptr;   // ne*2
+    int8_t* edge_slot = nullptr;   // ne*2
+};
+
+// quadrature description handed to the near-field kernel
+struct QuadDev {
+    double x[7][32], w[7][32];  // far, out, ang, rad, olam, omu, emu
+    int n[7];
+    int npan, opan, emupan;
+    double ratio, cf, kres, alen, oratio;
+};
+enum { QR_FAR = 0, QR_OUT, QR_ANG, QR_RAD, QR_OLAM, QR_OMU, QR_EMU };
+void make_quad(const sie_params& p, QuadDev& q);
+
+// One operator (one medium, one grid or near only)
+struct AimOp {
+    double kr = 0, ki = 0;          // wavenumber k = kr + j ki
+    bool has_grid = true;
+    GridDesc g{};
+    double2* spec = nullptr;        // 4 spectra (G, dG/dx, dG/dy, dG/dz), each n^3, scaled 1/n^3
+    float2* spec32 = nullptr;       // complex64 copy for the mixed path
+    int64_t npairs = 0;
+    int32_t* pairs = nullptr;       // device (t,s)
+    std::vector<int32_t> hpairs;
+    CsrPattern csr;
+    int64_t nnz = 0;
+    int64_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    double2* valL = nullptr;        // near-corrected L
+    double2* valK = nullptr;        // near-corrected K
+};
+
+struct Workspace {
+    size_t grid_elems = 0;          // n^3
+    double2* bufs = nullptr;        // 4 padded grids (n^3 each)
+    double2* src = nullptr;         // 4 compact grids (N^3 each)
+};
+
+}  // namespace sie
+
+struct sie_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+};
+
+struct sie_mesh {
+    sie_ctx* ctx = nullptr;
+    sie::HostMesh h;
+    sie::DevMesh d;
+};
+
+struct sie_op {
+    sie_mesh* mesh = nullptr;
+    sie_params p{};
+    double freq = 0, eps_r = 1, mu_r = 1, sigma = 0;
+    double k0 = 0;
+    sie::AimOp ext, inn;
+    int32_t* base = nullptr;        // stencil base (nt*3), shared by ext and inner grids
+    double* W = nullptr;            // weights nt * S * 4
+    sie::Workspace ws;
+    double2* xtmp = nullptr;        // scratch vectors (ne * 4)
+};
+
+// ------------------------------------------------------------------ launchers (aim.cu, near.cu)
+namespace sie {
+sie_status dev_upload_mesh(sie_mesh* m);
+sie_status dev_free_mesh(sie_mesh* m);
+sie_status aim_weights(sie_op* op);
+sie_status aim_spectra(sie_op* op, AimOp& a);
+sie_status near_build(sie_op* op, AimOp& a, const QuadDev& q);
+sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, double2* y);
+sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune);
+}  // namespace sie
