@@ -113,11 +113,21 @@ typedef struct {
 
 void sie_params_default(sie_params* p);
 
-/* Context on one CUDA device.  stream: a cudaStream_t to issue work on, or
- * NULL for a stream the context creates and owns. */
+/* Context on one CUDA device.  stream: the cudaStream_t every call of this
+ * context issues its device work on (NULL = the legacy default stream).  The
+ * stream is borrowed: the caller keeps it alive until sie_ctx_destroy. */
 sie_status sie_ctx_create(int device, void* stream, sie_ctx** out);
 sie_status sie_ctx_destroy(sie_ctx* ctx);
 const char* sie_last_error(void);
+
+/* Stage timers: while enabled, every kernel stage the context launches is
+ * bracketed by CUDA events on the context's stream, and its device time is
+ * accumulated under the stage's name.  Enabling clears the totals.
+ * sie_profile_read synchronises on the pending events and copies up to cap
+ * entries: names (cap x 32 chars, NUL terminated), total ms and launch
+ * counts; *n receives the number of stages seen. */
+sie_status sie_profile_enable(sie_ctx* ctx, int enable);
+sie_status sie_profile_read(sie_ctx* ctx, int cap, char* names, double* ms, int64_t* count, int* n);
 
 /* Mesh: xyz (nv x 3, metres), tri (nt x 3, 0-based, counter-clockwise seen
  * from outside).  Fails with SIE_ERR_MESH unless every edge is shared by
@@ -138,11 +148,13 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
                         const sie_params* params, sie_op** out);
 sie_status sie_op_destroy(sie_op* op);
 
-/* Operator facts.  info (12 doubles): [0..2] grid N_x, N_y, N_z; [3..5] FFT
+/* Operator facts.  info (16 doubles): [0..2] grid N_x, N_y, N_z; [3..5] FFT
  * n_x, n_y, n_z; [6] h; [7] near pairs (exterior); [8] nnz of the exterior
  * near matrix; [9] interior mode (0 = AIM, 1 = near only); [10] interior near
- * pairs; [11] grid origin x (origin y, z: see sie_op_grid). */
-sie_status sie_op_info(const sie_op* op, double info[12]);
+ * pairs; [11] grid origin x (origin y, z: see sie_op_grid); build wall times
+ * in ms: [12] weights and spectra, [13] exterior near region, [14] interior
+ * near region, [15] host-side pair lists. */
+sie_status sie_op_info(const sie_op* op, double info[16]);
 /* grid origin (3) and spacing of the exterior grid */
 sie_status sie_op_grid(const sie_op* op, double origin[3], double* h, int64_t N[3]);
 

@@ -41,6 +41,7 @@
 typedef double complex cplx;
 
 #define PI 3.14159265358979323846
+#define RCUT 36.0 /* exp(-36) < 1e-15 */
 
 typedef struct {
     const double *x, *w;
@@ -154,11 +155,11 @@ static int mu_rule(const qparams *qp, int graded, double *mx, double *mw)
 }
 
 static int tri_rule_graded(const double *apex, const double *b, const double *c, int toward_edge,
-                           const qparams *qp, const rule1d *rl, const rule1d *rm, double *pts,
-                           double *wts)
+                           int graded_mu, const qparams *qp, const rule1d *rl, const rule1d *rm,
+                           double *pts, double *wts)
 {
     double mx[256], mw[256];
-    int nmu = mu_rule(qp, toward_edge, mx, mw);
+    int nmu = mu_rule(qp, graded_mu, mx, mw);
     (void)rm;
     double e1[3], e2[3], nn[3];
     sub3(b, apex, e1);
@@ -219,7 +220,7 @@ static void inner_gauss(const double *r, const double *ipts, const double *iw, i
  * B_m = I R^m drho = (rhom Rm^m + m d^2 B_{m-2}) / (m + 1), B_0 = rhom,
  * B_-1 = asinh(rhom/|d|) (only ever needed times d^2, which is 0 at d = 0).
  * Lengths are scaled by Rmax.  Otherwise Gauss-Legendre on npan panels graded
- * geometrically toward rho = 0. */
+ * geometrically toward rho = 0, over rho <= RCUT/|Im k| (closed-form tail). */
 static void radial(cplx k, double rhom, double d, double Rmax, const qparams *qp, cplx *f1, cplx *f2)
 {
     if (cabs(k) * Rmax <= 1.0) {
@@ -262,20 +263,36 @@ static void radial(cplx k, double rhom, double d, double Rmax, const qparams *qp
         *f2 = s2;
         return;
     }
+    /* beyond R = RCUT/|Im k| the exponential is below 1e-15: there f1 has no
+     * contribution and (1 + jkR) exp(-jkR) - 1 = -1, whose integral is the
+     * static closed form S = log(rho + R) - rho/R */
+    double rc = rhom, tail = 0.0;
+    double kim = fabs(cimag(k));
+    if (kim > 0.0) {
+        double Rc = RCUT / kim, Rm = sqrt(rhom * rhom + d * d);
+        if (Rc < Rm) {
+            rc = Rc > fabs(d) ? sqrt(Rc * Rc - d * d) : 0.0;
+            double Rcc = sqrt(rc * rc + d * d);
+            tail = (log(rhom + Rm) - rhom / Rm) - (log(rc + Rcc) - rc / Rcc);
+        }
+    }
     cplx a1 = 0, a2 = 0;
-    double hi = rhom;
-    for (int p = 0; p < qp->npan; p++) {
+    double hi = rc;
+    for (int p = 0; p < qp->npan && rc > 0.0; p++) {
         double lo = (p == qp->npan - 1) ? 0.0 : hi * qp->pan_ratio;
         for (int q = 0; q < qp->rad.n; q++) {
             double rho = lo + (hi - lo) * qp->rad.x[q];
             double wr = (hi - lo) * qp->rad.w[q];
             double R = sqrt(rho * rho + d * d);
             cplx z = I * k * R;
-            a1 += wr * rho * rho * cexp(-z) / R;
-            a2 += wr * rho * rho * hfun(z) / (R * R * R);
+            cplx e = cexp(-z);
+            cplx hz = cabs(z) < 0.2 ? hfun(z) : (1.0 + z) * e - 1.0;
+            a1 += wr * rho * rho * e / R;
+            a2 += wr * rho * rho * hz / (R * R * R);
         }
         hi = lo;
     }
+    a2 -= tail;
     *f1 = a1;
     *f2 = a2;
 }
@@ -418,18 +435,18 @@ static void pair_moments(const double *V, const int *T, int t, int s, cplx k, co
     double *op = malloc(sizeof(double) * 3 * no), *ow = malloc(sizeof(double) * no);
     if (t != s && nsh == 2) {
         int ia = 3 - shared[0] - shared[1]; /* the vertex of t not on the shared edge */
-        no = tri_rule_graded(V + 3 * tt[ia], V + 3 * tt[(ia + 1) % 3], V + 3 * tt[(ia + 2) % 3], 1, qp,
+        no = tri_rule_graded(V + 3 * tt[ia], V + 3 * tt[(ia + 1) % 3], V + 3 * tt[(ia + 2) % 3], 1, 1, qp,
                              &qp->olaml, &qp->omul, op, ow);
     } else if (t != s && nsh == 1) {
         int ia = shared[0];
-        no = tri_rule_graded(V + 3 * tt[ia], V + 3 * tt[(ia + 1) % 3], V + 3 * tt[(ia + 2) % 3], 0, qp,
+        no = tri_rule_graded(V + 3 * tt[ia], V + 3 * tt[(ia + 1) % 3], V + 3 * tt[(ia + 2) % 3], 0, 0, qp,
                              &qp->olaml, &qp->omul, op, ow);
     } else if (t == s) {
         /* self pair: three sub-triangles from the centroid, graded toward the edges */
         no = 0;
         for (int i = 0; i < 3; i++)
-            no += tri_rule_graded(ct, V + 3 * tt[i], V + 3 * tt[(i + 1) % 3], 1, qp, &qp->olaml, &qp->omul,
-                                  op + 3 * no, ow + no);
+            no += tri_rule_graded(ct, V + 3 * tt[i], V + 3 * tt[(i + 1) % 3], 1, 1, qp, &qp->olaml,
+                                  &qp->omul, op + 3 * no, ow + no);
     } else {
         no = tri_rule(a, b, c, ro, op, ow);
     }

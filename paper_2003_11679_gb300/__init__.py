@@ -27,7 +27,8 @@ _STATUS = {0: "SIE_OK", 1: "SIE_ERR_ARG", 2: "SIE_ERR_MESH", 3: "SIE_ERR_OOM", 4
            5: "SIE_ERR_NOT_CONVERGED", 6: "SIE_ERR_TIMEOUT", 7: "SIE_ERR_STATE", 8: "SIE_ERR_UNSUPPORTED"}
 
 # every symbol the header declares
-SYMBOLS = ["sie_params_default", "sie_ctx_create", "sie_ctx_destroy", "sie_last_error", "sie_mesh_create",
+SYMBOLS = ["sie_params_default", "sie_ctx_create", "sie_ctx_destroy", "sie_last_error", "sie_profile_enable",
+           "sie_profile_read", "sie_mesh_create",
            "sie_mesh_destroy", "sie_mesh_counts", "sie_op_build", "sie_op_destroy", "sie_op_info", "sie_op_grid",
            "sie_matvec", "sie_op_near_csr", "sie_rhs_planewave", "sie_solve", "sie_rcs"]
 
@@ -64,6 +65,8 @@ def lib():
         L.sie_last_error.restype = ctypes.c_char_p
         L.sie_ctx_create.argtypes = [I, P, PP]
         L.sie_ctx_destroy.argtypes = [P]
+        L.sie_profile_enable.argtypes = [P, I]
+        L.sie_profile_read.argtypes = [P, I, P, P, P, P]
         L.sie_mesh_create.argtypes = [P, P, I64, P, I64, PP]
         L.sie_mesh_destroy.argtypes = [P]
         L.sie_mesh_counts.argtypes = [P, P]
@@ -116,6 +119,23 @@ class Context:
         s = ctypes.c_void_p(stream) if stream is not None else None
         _check(lib().sie_ctx_create(device, s, ctypes.byref(self.h)))
 
+    def profile(self, enable):
+        _check(lib().sie_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{stage: (total_ms, launches)} accumulated since profiling was enabled."""
+        cap = 64
+        names = ctypes.create_string_buffer(32 * cap)
+        ms = np.zeros(cap)
+        cnt = np.zeros(cap, np.int64)
+        n = ctypes.c_int()
+        _check(lib().sie_profile_read(self.h, cap, names, ms.ctypes.data, cnt.ctypes.data, ctypes.byref(n)))
+        out = {}
+        for i in range(min(n.value, cap)):
+            nm = names.raw[32 * i:32 * i + 32].split(b"\0")[0].decode()
+            out[nm] = (float(ms[i]), int(cnt[i]))
+        return out
+
     def close(self):
         if self.h:
             _check(lib().sie_ctx_destroy(self.h))
@@ -155,7 +175,7 @@ class Operator:
         _check(lib().sie_op_build(mesh.h, freq, eps_r, mu_r, sigma, ctypes.byref(p), ctypes.byref(self.h)))
 
     def info(self):
-        a = np.zeros(12)
+        a = np.zeros(16)
         _check(lib().sie_op_info(self.h, a.ctypes.data))
         return a
 

@@ -5,6 +5,7 @@
 //   pruned inverse FFT, interpolation W = P^T (gather), and the
 //   precorrected near-region CSR product (Eqs. LinNRP, KinNRP).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -259,7 +260,7 @@ static sie_status launch_pass(cudaStream_t st, int n, const double2* in, double2
 // full n grid already in buf) into the full spectrum in buf.
 // dir = +1: inverse of the spectrum in buf; prune = 1 writes only the physical
 // N box into the compact array `src` (used as output), prune = 0 keeps n^3 in buf.
-sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune)
+sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune, sie_ctx* pc)
 {
     const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int64_t Nx = prune ? g.N[0] : nx, Ny = prune ? g.N[1] : ny, Nz = prune ? g.N[2] : nz;
@@ -267,21 +268,39 @@ sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDe
     if (dir < 0) {
         // x pass: pencils (y < Ny, z < Nz)
         PassGeom X{(int)Nx, (int)nx, Ny * Nz, (int)Ny, prune ? Nx : nx, prune ? Nx * Ny : pyz, 1, nx, pyz, 1, 1};
-        SIE_TRY(launch_pass(st, (int)nx, prune ? src : buf, buf, 0, X));
+        {
+            Stage s_(pc, "fft_fwd_x");
+            SIE_TRY(launch_pass(st, (int)nx, prune ? src : buf, buf, 0, X));
+        }
         // y pass: pencils (x < nx, z < Nz)
         PassGeom Y{(int)Ny, (int)ny, nx * Nz, (int)nx, 1, pyz, nx, 1, pyz, nx, 0};
-        SIE_TRY(launch_pass(st, (int)ny, buf, buf, 0, Y));
+        {
+            Stage s_(pc, "fft_fwd_y");
+            SIE_TRY(launch_pass(st, (int)ny, buf, buf, 0, Y));
+        }
         // z pass: pencils (x < nx, y < ny)
         PassGeom Z{(int)Nz, (int)nz, nx * ny, (int)nx, 1, nx, pyz, 1, nx, pyz, 0};
-        SIE_TRY(launch_pass(st, (int)nz, buf, buf, 0, Z));
+        {
+            Stage s_(pc, "fft_fwd_z");
+            SIE_TRY(launch_pass(st, (int)nz, buf, buf, 0, Z));
+        }
     } else {
         PassGeom Z{(int)nz, (int)Nz, nx * ny, (int)nx, 1, nx, pyz, 1, nx, pyz, 0};
-        SIE_TRY(launch_pass(st, (int)nz, buf, buf, 1, Z));
+        {
+            Stage s_(pc, "fft_inv_z");
+            SIE_TRY(launch_pass(st, (int)nz, buf, buf, 1, Z));
+        }
         PassGeom Y{(int)ny, (int)Ny, nx * Nz, (int)nx, 1, pyz, nx, 1, pyz, nx, 0};
-        SIE_TRY(launch_pass(st, (int)ny, buf, buf, 1, Y));
+        {
+            Stage s_(pc, "fft_inv_y");
+            SIE_TRY(launch_pass(st, (int)ny, buf, buf, 1, Y));
+        }
         double2* dst = prune ? const_cast<double2*>(src) : buf;
         PassGeom X{(int)nx, (int)Nx, Ny * Nz, (int)Ny, nx, pyz, 1, prune ? Nx : nx, prune ? Nx * Ny : pyz, 1, 1};
-        SIE_TRY(launch_pass(st, (int)nx, buf, dst, 1, X));
+        {
+            Stage s_(pc, "fft_inv_x");
+            SIE_TRY(launch_pass(st, (int)nx, buf, dst, 1, X));
+        }
     }
     return SIE_OK;
 }
@@ -346,7 +365,7 @@ sie_status aim_spectra(sie_op* op, AimOp& a)
     SIE_CUDA_TRY(cudaMallocAsync((void**)&a.spec, sizeof(double2) * 4 * nn, st));
     k_sample<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(g, a.kr, a.ki, a.spec, nn);
     SIE_CUDA_TRY(cudaGetLastError());
-    for (int c = 0; c < 4; c++) SIE_TRY(fft3d(st, a.spec + c * nn, nullptr, g, -1, 0));
+    for (int c = 0; c < 4; c++) SIE_TRY(fft3d(st, a.spec + c * nn, nullptr, g, -1, 0, nullptr));
     return SIE_OK;
 }
 
@@ -507,7 +526,8 @@ __global__ void k_spmv(int nrow, const int64_t* __restrict__ rp, const int32_t* 
 // y = A x for one right-hand side, A = L (which_LK = 0) or K (1) of operator a
 sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, double2* y)
 {
-    cudaStream_t st = op->mesh->ctx->stream;
+    sie_ctx* pc = op->mesh->ctx;
+    cudaStream_t st = pc->stream;
     const DevMesh& M = op->mesh->d;
     SIE_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double2) * M.ne, st));
     if (a.has_grid) {
@@ -518,21 +538,33 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
         int ngrid = which_LK == 0 ? 4 : 3;
         double2* src = op->ws.src;
         double2* buf = op->ws.bufs;
-        SIE_CUDA_TRY(cudaMemsetAsync(src, 0, sizeof(double2) * ngrid * Ng, st));
-        k_project<<<(M.nt * S + 255) / 256, 256, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, x, g, ngrid, src, Ng);
-        SIE_CUDA_TRY(cudaGetLastError());
-        for (int c = 0; c < ngrid; c++) SIE_TRY(fft3d(st, buf + c * nn, src + c * Ng, g, -1, 1));
-        k_specmul<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(which_LK, a.spec, buf, nn);
-        SIE_CUDA_TRY(cudaGetLastError());
-        for (int c = 0; c < ngrid; c++) SIE_TRY(fft3d(st, buf + c * nn, src + c * Ng, g, +1, 1));
+        {
+            Stage s_(pc, "project");
+            SIE_CUDA_TRY(cudaMemsetAsync(src, 0, sizeof(double2) * ngrid * Ng, st));
+            k_project<<<(M.nt * S + 255) / 256, 256, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, x, g, ngrid, src, Ng);
+            SIE_CUDA_TRY(cudaGetLastError());
+        }
+        for (int c = 0; c < ngrid; c++) SIE_TRY(fft3d(st, buf + c * nn, src + c * Ng, g, -1, 1, pc));
+        {
+            Stage s_(pc, "specmul");
+            k_specmul<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(which_LK, a.spec, buf, nn);
+            SIE_CUDA_TRY(cudaGetLastError());
+        }
+        for (int c = 0; c < ngrid; c++) SIE_TRY(fft3d(st, buf + c * nn, src + c * Ng, g, +1, 1, pc));
         std::complex<double> kk(a.kr, a.ki);
         std::complex<double> sc = -1.0 / (kk * kk);
-        k_interp<<<(M.nt + 3) / 4, 128, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, src, g, which_LK == 0,
-                                                 make_double2(sc.real(), sc.imag()), Ng, y);
+        {
+            Stage s_(pc, "interp");
+            k_interp<<<(M.nt + 3) / 4, 128, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, src, g, which_LK == 0,
+                                                     make_double2(sc.real(), sc.imag()), Ng, y);
+            SIE_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    {
+        Stage s_(pc, a.has_grid ? "spmv_aim" : "spmv_near_only");
+        k_spmv<<<(M.ne + 3) / 4, 128, 0, st>>>(M.ne, a.row_ptr, a.col, which_LK == 0 ? a.valL : a.valK, x, y);
         SIE_CUDA_TRY(cudaGetLastError());
     }
-    k_spmv<<<(M.ne + 3) / 4, 128, 0, st>>>(M.ne, a.row_ptr, a.col, which_LK == 0 ? a.valL : a.valK, x, y);
-    SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
 }
 
@@ -615,12 +647,24 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
     op->ext.kr = op->k0;
     op->ext.ki = 0.0;
     op->ext.has_grid = true;
+    auto now = [] { return std::chrono::steady_clock::now(); };
+    auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+        return std::chrono::duration<double, std::milli>(b - a).count();
+    };
+    auto t0 = now();
     if ((s = aim_weights(op)) != SIE_OK) return fail(s);
     QuadDev q;
     make_quad(op->p, q);
     if ((s = aim_spectra(op, op->ext)) != SIE_OK) return fail(s);
+    cudaStreamSynchronize(st);
+    auto t1 = now();
+    op->build_ms[0] = ms(t0, t1);
     near_pairs_grid(mesh->h, g, hb, op->ext.hpairs);
+    auto t2 = now();
+    op->build_ms[3] = ms(t1, t2);
     if ((s = near_build(op, op->ext, q)) != SIE_OK) return fail(s);
+    auto t3 = now();
+    op->build_ms[1] = ms(t2, t3);
     // interior operator (Sec. III-C): near-only when every pair inside the
     // skin-depth cutoff is a near pair, else AIM on the object grid (shared
     // with the exterior grid for a single object)
@@ -637,7 +681,9 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
         if ((s = aim_spectra(op, op->inn)) != SIE_OK) return fail(s);
         op->inn.hpairs = op->ext.hpairs;
     }
+    auto t4 = now();
     if ((s = near_build(op, op->inn, q)) != SIE_OK) return fail(s);
+    op->build_ms[2] = ms(t4, now());
     // workspace
     int64_t nn = (int64_t)g.n[0] * g.n[1] * g.n[2], Ng = (int64_t)g.N[0] * g.N[1] * g.N[2];
     op->ws.grid_elems = nn;

@@ -337,6 +337,57 @@ void make_quad(const sie_params& p, QuadDev& q)
     q.oratio = p.q_oratio;
 }
 
+static cudaEvent_t prof_event(Prof& p)
+{
+    if (!p.pool.empty()) {
+        cudaEvent_t e = p.pool.back();
+        p.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+Stage::Stage(sie_ctx* ctx, const char* name) : c(ctx)
+{
+    if (!c || !c->prof.on) return;
+    Prof& p = c->prof;
+    for (size_t i = 0; i < p.names.size(); i++)
+        if (p.names[i] == name) id = (int)i;
+    if (id < 0) {
+        id = (int)p.names.size();
+        p.names.push_back(name);
+        p.ms.push_back(0.0);
+        p.count.push_back(0);
+    }
+    b = prof_event(p);
+    cudaEventRecord(b, c->stream);
+}
+
+Stage::~Stage()
+{
+    if (id < 0) return;
+    Prof& p = c->prof;
+    cudaEvent_t e = prof_event(p);
+    cudaEventRecord(e, c->stream);
+    p.pending.push_back({id, b, e});  // (start, end)
+}
+
+static void prof_drain(Prof& p)
+{
+    for (auto& r : p.pending) {
+        cudaEventSynchronize(r.b);
+        float t = 0;
+        cudaEventElapsedTime(&t, r.a, r.b);
+        p.ms[r.stage] += t;
+        p.count[r.stage] += 1;
+        p.pool.push_back(r.a);
+        p.pool.push_back(r.b);
+    }
+    p.pending.clear();
+}
+
 }  // namespace sie
 
 using namespace sie;
@@ -394,17 +445,8 @@ sie_status sie_ctx_create(int device, void* stream, sie_ctx** out)
     SIE_CUDA_TRY(cudaSetDevice(device));
     auto* c = new sie_ctx();
     c->device = device;
-    if (stream) {
-        c->stream = (cudaStream_t)stream;
-    } else {
-        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            delete c;
-            set_error(std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
-            return SIE_ERR_CUDA;
-        }
-        c->own_stream = true;
-    }
+    c->stream = (cudaStream_t)stream;  // NULL: the legacy default stream
+    c->own_stream = false;
     *out = c;
     return SIE_OK;
 }
@@ -413,8 +455,41 @@ sie_status sie_ctx_destroy(sie_ctx* ctx)
 {
     if (!ctx) return SIE_ERR_ARG;
     cudaSetDevice(ctx->device);
+    prof_drain(ctx->prof);
+    for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
+    return SIE_OK;
+}
+
+sie_status sie_profile_enable(sie_ctx* ctx, int enable)
+{
+    if (!ctx) return SIE_ERR_ARG;
+    SIE_CUDA_TRY(cudaSetDevice(ctx->device));
+    prof_drain(ctx->prof);
+    if (enable) {
+        std::fill(ctx->prof.ms.begin(), ctx->prof.ms.end(), 0.0);
+        std::fill(ctx->prof.count.begin(), ctx->prof.count.end(), 0);
+    }
+    ctx->prof.on = enable != 0;
+    return SIE_OK;
+}
+
+sie_status sie_profile_read(sie_ctx* ctx, int cap, char* names, double* ms, int64_t* count, int* n)
+{
+    if (!ctx || !n) return SIE_ERR_ARG;
+    SIE_CUDA_TRY(cudaSetDevice(ctx->device));
+    prof_drain(ctx->prof);
+    const Prof& p = ctx->prof;
+    *n = (int)p.names.size();
+    for (int i = 0; i < *n && i < cap; i++) {
+        if (names) {
+            std::strncpy(names + 32 * i, p.names[i].c_str(), 31);
+            names[32 * i + 31] = 0;
+        }
+        if (ms) ms[i] = p.ms[i];
+        if (count) count[i] = p.count[i];
+    }
     return SIE_OK;
 }
 
@@ -455,7 +530,7 @@ sie_status sie_mesh_counts(const sie_mesh* m, int64_t out[3])
     return SIE_OK;
 }
 
-sie_status sie_op_info(const sie_op* op, double info[12])
+sie_status sie_op_info(const sie_op* op, double info[16])
 {
     if (!op || !info) return SIE_ERR_ARG;
     const GridDesc& g = op->ext.g;
@@ -469,6 +544,7 @@ sie_status sie_op_info(const sie_op* op, double info[12])
     info[9] = op->inn.has_grid ? 0.0 : 1.0;
     info[10] = (double)op->inn.npairs;
     info[11] = g.o[0];
+    for (int i = 0; i < 4; i++) info[12 + i] = op->build_ms[i];
     return SIE_OK;
 }
 

@@ -130,11 +130,39 @@ struct Workspace {
 
 }  // namespace sie
 
+namespace sie {
+// CUDA-event stage timers on the context's stream (sie_profile_enable)
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+struct Prof {
+    bool on = false;
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<int64_t> count;
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> pool;
+};
+}  // namespace sie
+
 struct sie_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    sie::Prof prof;
 };
+
+namespace sie {
+// scoped stage timer: records events only while profiling is enabled
+struct Stage {
+    sie_ctx* c;
+    int id = -1;
+    cudaEvent_t b{};
+    Stage(sie_ctx* ctx, const char* name);
+    ~Stage();
+};
+}  // namespace sie
 
 struct sie_mesh {
     sie_ctx* ctx = nullptr;
@@ -152,6 +180,7 @@ struct sie_op {
     double* W = nullptr;            // weights nt * S * 4
     sie::Workspace ws;
     double2* xtmp = nullptr;        // scratch vectors (ne * 4)
+    double build_ms[4] = {0, 0, 0, 0};  // weights+spectra, exterior near, interior near, host lists
 };
 
 // ------------------------------------------------------------------ launchers (aim.cu, near.cu)
@@ -162,5 +191,6 @@ sie_status aim_weights(sie_op* op);
 sie_status aim_spectra(sie_op* op, AimOp& a);
 sie_status near_build(sie_op* op, AimOp& a, const QuadDev& q);
 sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, double2* y);
-sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune);
+sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune,
+                 sie_ctx* prof_ctx);
 }  // namespace sie

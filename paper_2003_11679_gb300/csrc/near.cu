@@ -23,6 +23,7 @@
 namespace sie {
 
 __constant__ QuadDev cq;
+#define RCUT 36.0  // exp(-36) < 1e-15
 
 // ------------------------------------------------------------------ complex helpers
 struct cd {
@@ -133,9 +134,21 @@ __device__ void radial(cd k, double rhom, double d, double Rmax, cd* f1, cd* f2)
         *f2 = s2;
         return;
     }
+    // beyond R = RCUT/|Im k| the exponential is below 1e-15: f1 has no
+    // contribution there and (1 + jkR) exp(-jkR) - 1 = -1 integrates in closed form
+    double rc = rhom, tail = 0.0;
+    double kim = fabs(k.im);
+    if (kim > 0.0) {
+        double Rc = RCUT / kim, Rm = sqrt(rhom * rhom + d * d);
+        if (Rc < Rm) {
+            rc = Rc > fabs(d) ? sqrt(Rc * Rc - d * d) : 0.0;
+            double Rcc = sqrt(rc * rc + d * d);
+            tail = (log(rhom + Rm) - rhom / Rm) - (log(rc + Rcc) - rc / Rcc);
+        }
+    }
     cd a1 = mk(0, 0), a2 = mk(0, 0);
-    double hi = rhom;
-    for (int p = 0; p < cq.npan; p++) {
+    double hi = rc;
+    for (int p = 0; p < cq.npan && rc > 0.0; p++) {
         double lo = (p == cq.npan - 1) ? 0.0 : hi * cq.ratio;
         for (int qq = 0; qq < cq.n[QR_RAD]; qq++) {
             double rho = lo + (hi - lo) * cq.x[QR_RAD][qq];
@@ -143,11 +156,13 @@ __device__ void radial(cd k, double rhom, double d, double Rmax, cd* f1, cd* f2)
             double R = sqrt(rho * rho + d * d);
             cd z = mk(-k.im * R, k.re * R);  // j k R
             cd e = cexpc(mk(-z.re, -z.im));
+            cd hz = cabsc(z) < 0.2 ? hfun(z) : (mk(1, 0) + z) * e - mk(1, 0);
             a1 = a1 + (wr * rho * rho / R) * e;
-            a2 = a2 + (wr * rho * rho / (R * R * R)) * hfun(z);
+            a2 = a2 + (wr * rho * rho / (R * R * R)) * hz;
         }
         hi = lo;
     }
+    a2 = a2 - mk(tail, 0);
     *f1 = a1;
     *f2 = a2;
 }
