@@ -93,6 +93,10 @@ typedef struct {
     int maxit;            /* outer iteration cap (800, Sec. V-A)                       */
     int restart;          /* GMRES restart length (100)                                */
     int inner_maxit;      /* nested iteration cap (200)                                */
+    double tol_constraint;/* constraint preconditioner: inner tolerance of its triangle
+                             (charge) system (1e-6)                                    */
+    int constraint_maxit; /* ... and its iteration cap (1000)                          */
+    int constraint_restart; /* ... and its GMRES restart length (100)                  */
     /* near-field quadrature (the method's direct-integration rule) */
     int q_far;            /* far-near pairs: q_far x q_far collapsed Gauss per triangle (5) */
     int q_out;            /* close pairs: q_out x q_out outer points (5)                */
@@ -147,6 +151,18 @@ sie_status sie_mesh_counts(const sie_mesh* mesh, int64_t out[3]);
 sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_r, double sigma,
                         const sie_params* params, sie_op** out);
 sie_status sie_op_destroy(sie_op* op);
+
+/* Replace the solver controls of a built operator: tol_outer, tol_inner,
+ * maxit, restart, inner_maxit, tol_constraint, constraint_maxit,
+ * constraint_restart are taken from params; grid and quadrature fields are
+ * ignored (they are fixed at build time). */
+sie_status sie_op_set_solver(sie_op* op, const sie_params* params);
+
+/* Statistics of the last sie_solve on this operator (6 doubles): outer
+ * iterations, outer relative residual, the largest nested (interior)
+ * iteration count and residual, the largest constraint-preconditioner
+ * iteration count and residual. */
+sie_status sie_op_stats(const sie_op* op, double out[6]);
 
 /* Operator facts.  info (16 doubles): [0..2] grid N_x, N_y, N_z; [3..5] FFT
  * n_x, n_y, n_z; [6] h; [7] near pairs (exterior); [8] nnz of the exterior

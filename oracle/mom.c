@@ -212,6 +212,41 @@ static void inner_gauss(const double *r, const double *ipts, const double *iw, i
 }
 
 
+/* Ein(z) = I_0^z (1 - exp(-t))/t dt, Re z >= 0: power series for |z| < 2,
+ * otherwise E1(z) + log z + Euler's gamma with E1 from its continued
+ * fraction e^-z / (z + 1/(1 + 1/(z + 2/(1 + 2/(z + ...))))) (modified Lentz). */
+static cplx ein(cplx z)
+{
+    if (cabs(z) < 2.0) {
+        cplx s = 0.0, t = 1.0;
+        for (int n = 1; n < 60; n++) {
+            t *= z / (double)n; /* z^n / n! */
+            cplx term = ((n % 2) ? 1.0 : -1.0) * t / (double)n;
+            s += term;
+            if (cabs(term) < 1e-17 * cabs(s)) break;
+        }
+        return s;
+    }
+    /* Lentz on b0 + a1/(b1 + a2/(b2 + ...)) with b = z, 1, z, 1, ... and
+     * a = 1, 1, 1, 2, 2, 3, 3, ... */
+    const double tiny = 1e-300;
+    cplx f = z, C = z, D = 0.0;
+    for (int i = 1; i < 500; i++) {
+        double a = (double)((i + 1) / 2);
+        cplx b = (i % 2) ? 1.0 : z;
+        D = b + a * D;
+        if (cabs(D) < tiny) D = tiny;
+        C = b + a / C;
+        if (cabs(C) < tiny) C = tiny;
+        D = 1.0 / D;
+        cplx delta = C * D;
+        f *= delta;
+        if (cabs(delta - 1.0) < 1e-16) break;
+    }
+    const double euler = 0.57721566490153286061;
+    return cexp(-z) / f + clog(z) + euler;
+}
+
 /* Bounded radial remainders of the polar scheme at one angle:
  *   f1 = I_0^rhom rho^2 exp(-jkR)/R drho,
  *   f2 = I_0^rhom rho^2 [(1 + jkR) exp(-jkR) - 1]/R^3 drho,   R^2 = rho^2 + d^2.
@@ -263,6 +298,14 @@ static void radial(cplx k, double rhom, double d, double Rmax, const qparams *qp
         *f2 = s2;
         return;
     }
+    if (d == 0.0) {
+        /* coplanar point: closed forms, z = j k rhom:
+         * f1 = I rho exp(-jk rho) drho, f2 = 1 - exp(-z) - Ein(z) */
+        cplx z = I * k * rhom, e = cexp(-z);
+        *f1 = (1.0 - e * (1.0 + z)) / ((I * k) * (I * k));
+        *f2 = 1.0 - e - ein(z);
+        return;
+    }
     /* beyond R = RCUT/|Im k| the exponential is below 1e-15: there f1 has no
      * contribution and (1 + jkR) exp(-jkR) - 1 = -1, whose integral is the
      * static closed form S = log(rho + R) - rho/R */
@@ -310,16 +353,33 @@ static void inner_polar(const double *r, const double *v0, const double *v1, con
     double rv0[3];
     sub3(r, v0, rv0);
     double dd = dot3(rv0, nrm);
-    double ad = fabs(dd);
     double rho0[3];
     for (int d = 0; d < 3; d++) rho0[d] = r[d] - dd * nrm[d];
 
-    double Rmax = 0.0; /* farthest vertex: bounds R over the triangle */
+    double Rmax = 0.0, Rmin = 1e300; /* farthest / nearest vertex */
     for (int i = 0; i < 3; i++) {
         double dv[3];
         sub3(vv[i], r, dv);
         double rr = norm3(dv);
         if (rr > Rmax) Rmax = rr;
+        if (rr < Rmin) Rmin = rr;
+    }
+    if (fabs(dd) < 1e-12 * Rmax) dd = 0.0; /* on the plane up to rounding */
+    double ad = fabs(dd);
+    memset(o, 0, sizeof(*o));
+    /* whole triangle beyond RCUT/|Im k|: every term below exp(-RCUT) */
+    double kim = fabs(cimag(k));
+    if (kim > 0.0) {
+        double c[3] = {(v0[0] + v1[0] + v2[0]) / 3.0, (v0[1] + v1[1] + v2[1]) / 3.0, (v0[2] + v1[2] + v2[2]) / 3.0};
+        double rc = 0.0, dc[3];
+        for (int i = 0; i < 3; i++) {
+            double dv[3];
+            sub3(vv[i], c, dv);
+            double q = norm3(dv);
+            if (q > rc) rc = q;
+        }
+        sub3(r, c, dc);
+        if (norm3(dc) - rc > RCUT / kim) return;
     }
     cplx Is = 0, Iv[3] = {0, 0, 0}, Ign = 0, Igt[3] = {0, 0, 0};
     double Omega = 0.0;

@@ -11,7 +11,7 @@ n x L[.] and n x K[.] equals RWG testing of the tangential fields):
   LA_mn = II f_m . f_n G,     Lphi_pq = II_{T_p x T_q} G / (A_p A_q)
   so that L = LA - k^-2 D^T Lphi D  with D the signed edge-length incidence.
   K_mn  = I f_m . PV I grad G x f_n dS' dS                     (Eq. (opK))
-  Ix_mn = I (n x f_m) . f_n dS                                  (Sec. II-A)
+  Ix_mn = I f_m . (n x f_n) dS                                  (Sec. II-A)
 
 The near-field integration rule (the paper only says "direct integration")
 is fixed by QUAD below and implemented in mom.c.
@@ -171,9 +171,13 @@ def local_entries(mesh, t, s, M, k):
 
 
 def Ix(mesh):
-    """Dense I_x: (Ix)_mn = I_T (n x f_m) . f_n dS, nonzero only when m, n share a
-    triangle.  With origin at the centroid (where I (r - c) dS = 0) the
-    triangle integral is closed form: c_m c_n A n . ((p_m - c) x (p_n - c))."""
+    """Dense I_x of Eqs. (MFIE1dis), (EFIE01dis): (Ix)_mn = I_T f_m . (n x f_n) dS,
+    nonzero only when m, n share a triangle.  This orientation is the one for
+    which the paper's signs (K_i - Ix/2 inside, K_0 + Ix/2 outside, -E_inc on
+    the right) reproduce the Mie series (tests/test_system_oracle.py); the
+    opposite orientation gives a 7x wrong RCS.  With origin at the centroid
+    (where I (r - c) dS = 0) the integral is closed form:
+    c_m c_n A n . ((p_n - c) x (p_m - c))."""
     ne = mesh.ne
     X = np.zeros((ne, ne))
     cf = mesh.coef()
@@ -182,6 +186,6 @@ def Ix(mesh):
         p = mesh.V[mesh.tri_free[t]] - c
         for i in range(3):
             for j in range(3):
-                val = cf[t, i] * cf[t, j] * mesh.area[t] * (mesh.normal[t] @ np.cross(p[i], p[j]))
+                val = cf[t, i] * cf[t, j] * mesh.area[t] * (mesh.normal[t] @ np.cross(p[j], p[i]))
                 X[mesh.tri_edge[t, i], mesh.tri_edge[t, j]] += val
     return X

@@ -29,7 +29,8 @@ _STATUS = {0: "SIE_OK", 1: "SIE_ERR_ARG", 2: "SIE_ERR_MESH", 3: "SIE_ERR_OOM", 4
 # every symbol the header declares
 SYMBOLS = ["sie_params_default", "sie_ctx_create", "sie_ctx_destroy", "sie_last_error", "sie_profile_enable",
            "sie_profile_read", "sie_mesh_create",
-           "sie_mesh_destroy", "sie_mesh_counts", "sie_op_build", "sie_op_destroy", "sie_op_info", "sie_op_grid",
+           "sie_mesh_destroy", "sie_mesh_counts", "sie_op_build", "sie_op_destroy", "sie_op_set_solver",
+           "sie_op_stats", "sie_op_info", "sie_op_grid",
            "sie_matvec", "sie_op_near_csr", "sie_rhs_planewave", "sie_solve", "sie_rcs"]
 
 
@@ -38,6 +39,8 @@ class sie_params(ctypes.Structure):
                 ("stencil_order", ctypes.c_int), ("near_radius", ctypes.c_int), ("skin_cutoff", ctypes.c_double),
                 ("precision", ctypes.c_int), ("tol_outer", ctypes.c_double), ("tol_inner", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("inner_maxit", ctypes.c_int),
+                ("tol_constraint", ctypes.c_double), ("constraint_maxit", ctypes.c_int),
+                ("constraint_restart", ctypes.c_int),
                 ("q_far", ctypes.c_int), ("q_out", ctypes.c_int), ("q_ang", ctypes.c_int), ("q_rad", ctypes.c_int),
                 ("q_npan", ctypes.c_int), ("q_opan", ctypes.c_int), ("q_olam", ctypes.c_int),
                 ("q_omu", ctypes.c_int), ("q_emupan", ctypes.c_int), ("q_emu", ctypes.c_int),
@@ -72,6 +75,8 @@ def lib():
         L.sie_mesh_counts.argtypes = [P, P]
         L.sie_op_build.argtypes = [P, D, D, D, D, ctypes.POINTER(sie_params), PP]
         L.sie_op_destroy.argtypes = [P]
+        L.sie_op_set_solver.argtypes = [P, ctypes.POINTER(sie_params)]
+        L.sie_op_stats.argtypes = [P, P]
         L.sie_op_info.argtypes = [P, P]
         L.sie_op_grid.argtypes = [P, P, P, P]
         L.sie_matvec.argtypes = [P, I, P, P, I, I]
@@ -206,6 +211,47 @@ class Operator:
         _check(lib().sie_op_near_csr(self.h, which, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
                                      ctypes.byref(nnz)))
         return rp, col, val
+
+    def set_solver(self, **kw):
+        _check(lib().sie_op_set_solver(self.h, ctypes.byref(params(**kw))))
+
+    def stats(self):
+        a = np.zeros(6)
+        _check(lib().sie_op_stats(self.h, a.ctypes.data))
+        return dict(iters=int(a[0]), relres=a[1], inner_iters_max=int(a[2]), inner_relres_max=a[3],
+                    constraint_iters_max=int(a[4]), constraint_relres_max=a[5])
+
+    def rhs_planewave(self, khat, epol, out=None):
+        """b = [-(1/eta0) <f_m, E_inc>; 0] (length N_e + N_t per right-hand side)."""
+        kh = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+        ep = np.ascontiguousarray(np.atleast_2d(epol), dtype=np.float64)
+        nrhs = len(kh)
+        n = self.mesh.ne + self.mesh.nt
+        b = out if out is not None else np.zeros((nrhs, n) if nrhs > 1 else n, np.complex128)
+        pb, dev = _ptr(b)
+        _check(lib().sie_rhs_planewave(self.h, kh.ctypes.data, ep.ctypes.data, nrhs, pb,
+                                       SIE_DEVICE_PTRS if dev else 0))
+        return b
+
+    def solve(self, b, x=None, nrhs=1, check=True):
+        """x = SYS^-1 b by FGMRES; returns (x, iters, relres)."""
+        if x is None:
+            x = np.zeros_like(b)
+        pb, db = _ptr(b)
+        px, dx = _ptr(x)
+        it = np.zeros(nrhs, np.int32)
+        rr = np.zeros(nrhs)
+        code = lib().sie_solve(self.h, pb, px, nrhs, it.ctypes.data, rr.ctypes.data, SIE_DEVICE_PTRS if db else 0)
+        if check or code != SIE_ERR_NOT_CONVERGED:
+            _check(code)
+        return x, it, rr
+
+    def rcs(self, x, rhat):
+        rh = np.ascontiguousarray(np.atleast_2d(rhat), dtype=np.float64)
+        out = np.zeros(len(rh))
+        px, dx = _ptr(x)
+        _check(lib().sie_rcs(self.h, px, rh.ctypes.data, len(rh), out.ctypes.data, SIE_DEVICE_PTRS if dx else 0))
+        return out
 
     def close(self):
         if self.h:

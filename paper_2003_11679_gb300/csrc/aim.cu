@@ -523,6 +523,19 @@ __global__ void k_spmv(int nrow, const int64_t* __restrict__ rp, const int32_t* 
     }
 }
 
+// y += W applied to the inverse-transformed grids (3 vector grids, + scalar grid)
+sie_status aim_interp(sie_op* op, const double2* grids, int has_phi, double2 scal, double2* y)
+{
+    const DevMesh& M = op->mesh->d;
+    const GridDesc& g = op->ext.g;
+    int S = (g.M + 1) * (g.M + 1) * (g.M + 1);
+    int64_t Ng = (int64_t)g.N[0] * g.N[1] * g.N[2];
+    k_interp<<<(M.nt + 3) / 4, 128, 0, op->mesh->ctx->stream>>>(M.nt, S, g.M, M, op->base, op->W, grids, g, has_phi,
+                                                                scal, Ng, y);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
 // y = A x for one right-hand side, A = L (which_LK = 0) or K (1) of operator a
 sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, double2* y)
 {
@@ -555,9 +568,7 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
         std::complex<double> sc = -1.0 / (kk * kk);
         {
             Stage s_(pc, "interp");
-            k_interp<<<(M.nt + 3) / 4, 128, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, src, g, which_LK == 0,
-                                                     make_double2(sc.real(), sc.imag()), Ng, y);
-            SIE_CUDA_TRY(cudaGetLastError());
+            SIE_TRY(aim_interp(op, src, which_LK == 0, make_double2(sc.real(), sc.imag()), y));
         }
     }
     {
@@ -570,9 +581,13 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
 
 static void free_aim(AimOp& a)
 {
-    void* ptrs[] = {a.spec, a.spec32, a.pairs, a.row_ptr, a.col, a.valL, a.valK};
+    void* ptrs[] = {a.spec, a.spec32, a.pairs, a.row_ptr, a.col, a.valL, a.valK, a.valLA, a.dLA, a.dL,
+                    a.tri_row_ptr, a.tri_col, a.valLphi, a.valLphiNR};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    a.valLA = a.dLA = a.dL = a.valLphi = a.valLphiNR = nullptr;
+    a.tri_row_ptr = nullptr;
+    a.tri_col = nullptr;
     a.spec = nullptr;
     a.spec32 = nullptr;
     a.pairs = nullptr;
@@ -592,6 +607,7 @@ sie_status sie_op_destroy(sie_op* op)
     if (!op) return SIE_ERR_ARG;
     cudaSetDevice(op->mesh->ctx->device);
     cudaStreamSynchronize(op->mesh->ctx->stream);
+    sys_release(op);
     free_aim(op->ext);
     free_aim(op->inn);
     void* ptrs[] = {op->base, op->W, op->ws.bufs, op->ws.src, op->xtmp};
@@ -687,13 +703,14 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
     // workspace
     int64_t nn = (int64_t)g.n[0] * g.n[1] * g.n[2], Ng = (int64_t)g.N[0] * g.N[1] * g.N[2];
     op->ws.grid_elems = nn;
-    cudaError_t e1 = cudaMallocAsync((void**)&op->ws.bufs, sizeof(double2) * 4 * nn, st);
-    cudaError_t e2 = cudaMallocAsync((void**)&op->ws.src, sizeof(double2) * 4 * Ng, st);
+    cudaError_t e1 = cudaMallocAsync((void**)&op->ws.bufs, sizeof(double2) * 7 * nn, st);
+    cudaError_t e2 = cudaMallocAsync((void**)&op->ws.src, sizeof(double2) * 7 * Ng, st);
     cudaError_t e3 = cudaMallocAsync((void**)&op->xtmp, sizeof(double2) * 4 * mesh->h.ne, st);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
         set_error("sie_op_build: workspace allocation failed");
         return fail(SIE_ERR_OOM);
     }
+    if ((s = sys_prepare(op)) != SIE_OK) return fail(s);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         set_error(std::string("sie_op_build: ") + cudaGetErrorString(e));
@@ -705,35 +722,36 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
 
 sie_status sie_matvec(sie_op* op, int which, const double* x, double* y, int nrhs, int flags)
 {
-    if (!op || !x || !y || nrhs < 1) {
+    if (!op || !x || !y || nrhs < 1 || which < SIE_OP_L0 || which > SIE_OP_ZI) {
         set_error("sie_matvec: invalid argument");
         return SIE_ERR_ARG;
     }
-    if (which < SIE_OP_L0 || which > SIE_OP_KI) {
-        set_error("sie_matvec: operator not available in this build");
-        return SIE_ERR_UNSUPPORTED;
-    }
     SIE_CUDA_TRY(cudaSetDevice(op->mesh->ctx->device));
     cudaStream_t st = op->mesh->ctx->stream;
-    const int64_t ne = op->mesh->h.ne;
-    AimOp& a = (which == SIE_OP_L0 || which == SIE_OP_K0) ? op->ext : op->inn;
-    int lk = (which == SIE_OP_L0 || which == SIE_OP_LI) ? 0 : 1;
+    const int64_t ne = op->mesh->h.ne, nt = op->mesh->h.nt;
+    const int64_t len = which == SIE_OP_SYS ? ne + nt : ne;
     bool dev = flags & SIE_DEVICE_PTRS;
     for (int r = 0; r < nrhs; r++) {
         const double2* xr;
         double2* yr;
         if (dev) {
-            xr = (const double2*)x + r * ne;
-            yr = (double2*)y + r * ne;
+            xr = (const double2*)x + r * len;
+            yr = (double2*)y + r * len;
         } else {
-            SIE_CUDA_TRY(cudaMemcpyAsync(op->xtmp, (const double2*)x + r * ne, sizeof(double2) * ne,
+            SIE_CUDA_TRY(cudaMemcpyAsync(op->sys_vec, (const double2*)x + r * len, sizeof(double2) * len,
                                          cudaMemcpyHostToDevice, st));
-            xr = op->xtmp;
-            yr = op->xtmp + ne;
+            xr = op->sys_vec;
+            yr = op->sys_vec + len;
         }
-        SIE_TRY(aim_apply(op, a, lk, xr, yr));
+        if (which >= SIE_OP_SYS) {
+            SIE_TRY(sys_matvec(op, which, xr, yr));
+        } else {
+            AimOp& a = (which == SIE_OP_L0 || which == SIE_OP_K0) ? op->ext : op->inn;
+            int lk = (which == SIE_OP_L0 || which == SIE_OP_LI) ? 0 : 1;
+            SIE_TRY(aim_apply(op, a, lk, xr, yr));
+        }
         if (!dev)
-            SIE_CUDA_TRY(cudaMemcpyAsync((double2*)y + r * ne, yr, sizeof(double2) * ne, cudaMemcpyDeviceToHost, st));
+            SIE_CUDA_TRY(cudaMemcpyAsync((double2*)y + r * len, yr, sizeof(double2) * len, cudaMemcpyDeviceToHost, st));
     }
     if (!dev) SIE_CUDA_TRY(cudaStreamSynchronize(st));
     return SIE_OK;
@@ -757,22 +775,77 @@ sie_status sie_op_near_csr(const sie_op* op, int which, int64_t* row_ptr, int32_
     return SIE_OK;
 }
 
-sie_status sie_rhs_planewave(sie_op*, const double*, const double*, int, double*, int)
+sie_status sie_rhs_planewave(sie_op* op, const double* khat, const double* epol, int nrhs, double* b, int flags)
 {
-    set_error("sie_rhs_planewave: not available in this build");
-    return SIE_ERR_UNSUPPORTED;
+    if (!op || !khat || !epol || !b || nrhs < 1) {
+        set_error("sie_rhs_planewave: invalid argument");
+        return SIE_ERR_ARG;
+    }
+    SIE_CUDA_TRY(cudaSetDevice(op->mesh->ctx->device));
+    cudaStream_t st = op->mesh->ctx->stream;
+    const int64_t len = op->mesh->h.ne + op->mesh->h.nt;
+    for (int r = 0; r < nrhs; r++) {
+        double2* br = (flags & SIE_DEVICE_PTRS) ? (double2*)b + r * len : op->sys_vec;
+        SIE_TRY(sys_rhs(op, khat + 3 * r, epol + 3 * r, br));
+        if (!(flags & SIE_DEVICE_PTRS))
+            SIE_CUDA_TRY(cudaMemcpyAsync((double2*)b + r * len, br, sizeof(double2) * len, cudaMemcpyDeviceToHost, st));
+    }
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIE_OK;
 }
 
-sie_status sie_solve(sie_op*, const double*, double*, int, int*, double*, int)
+sie_status sie_solve(sie_op* op, const double* b, double* x, int nrhs, int* iters, double* relres, int flags)
 {
-    set_error("sie_solve: not available in this build");
-    return SIE_ERR_UNSUPPORTED;
+    if (!op || !b || !x || nrhs < 1) {
+        set_error("sie_solve: invalid argument");
+        return SIE_ERR_ARG;
+    }
+    SIE_CUDA_TRY(cudaSetDevice(op->mesh->ctx->device));
+    cudaStream_t st = op->mesh->ctx->stream;
+    const int64_t len = op->mesh->h.ne + op->mesh->h.nt;
+    sie_status worst = SIE_OK;
+    for (int r = 0; r < nrhs; r++) {
+        const double2* br;
+        double2* xr;
+        if (flags & SIE_DEVICE_PTRS) {
+            br = (const double2*)b + r * len;
+            xr = (double2*)x + r * len;
+        } else {
+            SIE_CUDA_TRY(cudaMemcpyAsync(op->sys_vec + 2 * len, (const double2*)b + r * len, sizeof(double2) * len,
+                                         cudaMemcpyHostToDevice, st));
+            br = op->sys_vec + 2 * len;
+            xr = op->sys_vec + 3 * len;
+        }
+        int it = 0;
+        double rr = 0;
+        sie_status s = sys_solve(op, br, xr, &it, &rr);
+        if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
+        if (s == SIE_ERR_NOT_CONVERGED) worst = s;
+        if (iters) iters[r] = it;
+        if (relres) relres[r] = rr;
+        if (!(flags & SIE_DEVICE_PTRS))
+            SIE_CUDA_TRY(cudaMemcpyAsync((double2*)x + r * len, xr, sizeof(double2) * len, cudaMemcpyDeviceToHost, st));
+    }
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (worst != SIE_OK) set_error("sie_solve: GMRES reached maxit before the tolerance");
+    return worst;
 }
 
-sie_status sie_rcs(sie_op*, const double*, const double*, int, double*, int)
+sie_status sie_rcs(sie_op* op, const double* x, const double* rhat, int ndir, double* rcs, int flags)
 {
-    set_error("sie_rcs: not available in this build");
-    return SIE_ERR_UNSUPPORTED;
+    if (!op || !x || !rhat || !rcs || ndir < 1) {
+        set_error("sie_rcs: invalid argument");
+        return SIE_ERR_ARG;
+    }
+    SIE_CUDA_TRY(cudaSetDevice(op->mesh->ctx->device));
+    cudaStream_t st = op->mesh->ctx->stream;
+    const int64_t len = op->mesh->h.ne + op->mesh->h.nt;
+    const double2* xr = (const double2*)x;
+    if (!(flags & SIE_DEVICE_PTRS)) {
+        SIE_CUDA_TRY(cudaMemcpyAsync(op->sys_vec, x, sizeof(double2) * len, cudaMemcpyHostToDevice, st));
+        xr = op->sys_vec;
+    }
+    return sys_rcs(op, xr, rhat, ndir, rcs);
 }
 
 }  // extern "C"

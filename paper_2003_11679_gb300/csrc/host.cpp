@@ -411,6 +411,9 @@ void sie_params_default(sie_params* p)
     p->maxit = 800;
     p->restart = 100;
     p->inner_maxit = 200;
+    p->tol_constraint = 1e-6;
+    p->constraint_maxit = 1000;
+    p->constraint_restart = 100;
     p->q_far = 5;
     p->q_out = 5;
     p->q_ang = 8;
@@ -545,6 +548,31 @@ sie_status sie_op_info(const sie_op* op, double info[16])
     info[10] = (double)op->inn.npairs;
     info[11] = g.o[0];
     for (int i = 0; i < 4; i++) info[12 + i] = op->build_ms[i];
+    return SIE_OK;
+}
+
+sie_status sie_op_set_solver(sie_op* op, const sie_params* p)
+{
+    if (!op || !p || !(p->tol_outer > 0) || !(p->tol_inner > 0) || p->maxit < 1 || p->restart < 1 ||
+        p->inner_maxit < 1 || !(p->tol_constraint > 0) || p->constraint_maxit < 1 || p->constraint_restart < 1) {
+        set_error("sie_op_set_solver: invalid argument");
+        return SIE_ERR_ARG;
+    }
+    op->p.tol_outer = p->tol_outer;
+    op->p.tol_inner = p->tol_inner;
+    op->p.maxit = p->maxit;
+    op->p.restart = p->restart;
+    op->p.inner_maxit = p->inner_maxit;
+    op->p.tol_constraint = p->tol_constraint;
+    op->p.constraint_maxit = p->constraint_maxit;
+    op->p.constraint_restart = p->constraint_restart;
+    return SIE_OK;
+}
+
+sie_status sie_op_stats(const sie_op* op, double out[6])
+{
+    if (!op || !out) return SIE_ERR_ARG;
+    for (int i = 0; i < 6; i++) out[i] = op->stats[i];
     return SIE_OK;
 }
 

@@ -120,6 +120,16 @@ struct AimOp {
     int32_t* col = nullptr;
     double2* valL = nullptr;        // near-corrected L
     double2* valK = nullptr;        // near-corrected K
+    double2* valLA = nullptr;       // near-corrected LA (vector potential part)
+    double2* dLA = nullptr;         // exact diagonal of LA
+    double2* dL = nullptr;          // exact diagonal of L
+    // triangle CSR of the near-corrected Lphi (pairs in (t, s) order)
+    std::vector<int64_t> tri_row_ptr_h;
+    std::vector<int32_t> tri_col_h;
+    int64_t* tri_row_ptr = nullptr;
+    int32_t* tri_col = nullptr;
+    double2* valLphi = nullptr;
+    double2* valLphiNR = nullptr;   // exact near Lphi (constraint preconditioner)
 };
 
 struct Workspace {
@@ -170,6 +180,17 @@ struct sie_mesh {
     sie::DevMesh d;
 };
 
+namespace sie {
+// Krylov workspace of one restarted FGMRES (basis V, preconditioned basis Z)
+struct KrylovWork {
+    int64_t n = 0;
+    int m = 0;
+    double2 *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *r = nullptr;
+    sie_status alloc(cudaStream_t st, int64_t n_, int m_);
+    void release(cudaStream_t st);
+};
+}  // namespace sie
+
 struct sie_op {
     sie_mesh* mesh = nullptr;
     sie_params p{};
@@ -181,6 +202,18 @@ struct sie_op {
     sie::Workspace ws;
     double2* xtmp = nullptr;        // scratch vectors (ne * 4)
     double build_ms[4] = {0, 0, 0, 0};  // weights+spectra, exterior near, interior near, host lists
+    // system operator (Eq. sys)
+    int64_t* ix_row_ptr = nullptr;  // Ix as edge CSR (real values stored as double2)
+    int32_t* ix_col = nullptr;
+    double2* ix_val = nullptr;
+    double* elen = nullptr;         // edge lengths
+    double2* sys_E = nullptr;       // E' = Z' H (ne)
+    double2* sys_tmp = nullptr;     // ne + 2 nt scratch
+    double2* sys_vec = nullptr;     // 4 (ne + nt) scratch for host-pointer calls
+    sie::KrylovWork kin, kout, kcs_in, kcs_out;
+    double2 *cs_e = nullptr, *cs_t = nullptr, *pc_e = nullptr, *pc_t = nullptr;  // preconditioner scratch
+    // last solve: outer iters, relres; max nested iters, relres; max constraint iters, relres
+    double stats[6] = {0, 0, 0, 0, 0, 0};
 };
 
 // ------------------------------------------------------------------ launchers (aim.cu, near.cu)
@@ -191,6 +224,13 @@ sie_status aim_weights(sie_op* op);
 sie_status aim_spectra(sie_op* op, AimOp& a);
 sie_status near_build(sie_op* op, AimOp& a, const QuadDev& q);
 sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, double2* y);
+sie_status aim_interp(sie_op* op, const double2* grids, int has_phi, double2 scal, double2* y);
+sie_status sys_prepare(sie_op* op);
+void sys_release(sie_op* op);
+sie_status sys_matvec(sie_op* op, int which, const double2* x, double2* y);
+sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres);
+sie_status sys_rhs(sie_op* op, const double* khat, const double* epol, double2* b);
+sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, double* rcs);
 sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune,
                  sie_ctx* prof_ctx);
 }  // namespace sie

@@ -23,6 +23,9 @@
 namespace sie {
 
 __constant__ QuadDev cq;
+// per near pair: [0..8] LA exact-grid, [9..17] K exact-grid, [18] Lphi exact-grid,
+// [19..27] LA exact, [28] Lphi exact
+#define NLOC 29
 #define RCUT 36.0  // exp(-36) < 1e-15
 
 // ------------------------------------------------------------------ complex helpers
@@ -96,6 +99,40 @@ struct Inner {
     cd Ig[3];
 };
 
+__device__ __forceinline__ cd clogc(cd z) { return mk(log(hypot(z.re, z.im)), atan2(z.im, z.re)); }
+
+// Ein(z) = I_0^z (1 - exp(-t))/t dt for Re z >= 0: series for |z| < 2, else
+// E1(z) + log z + gamma, E1 by its continued fraction (modified Lentz)
+__device__ cd ein(cd z)
+{
+    if (cabsc(z) < 2.0) {
+        cd s = mk(0, 0), t = mk(1, 0);
+        for (int n = 1; n < 60; n++) {
+            t = t * z * (1.0 / (double)n);
+            cd term = ((n & 1) ? 1.0 : -1.0) / (double)n * t;
+            s = s + term;
+            if (cabsc(term) < 1e-17 * cabsc(s)) break;
+        }
+        return s;
+    }
+    const double tiny = 1e-300;
+    cd f = z, C = z, D = mk(0, 0);
+    for (int i = 1; i < 500; i++) {
+        double a = (double)((i + 1) / 2);
+        cd b = (i & 1) ? mk(1, 0) : z;
+        D = b + a * D;
+        if (cabsc(D) < tiny) D = mk(tiny, 0);
+        C = b + cdivc(mk(a, 0), C);
+        if (cabsc(C) < tiny) C = mk(tiny, 0);
+        D = cdivc(mk(1, 0), D);
+        cd delta = C * D;
+        f = f * delta;
+        if (cabsc(delta - mk(1, 0)) < 1e-16) break;
+    }
+    const double euler = 0.57721566490153286061;
+    return cdivc(cexpc(mk(-z.re, -z.im)), f) + clogc(z) + mk(euler, 0);
+}
+
 // bounded radial remainders (series when |k| Rmax <= 1, else graded Gauss)
 __device__ void radial(cd k, double rhom, double d, double Rmax, cd* f1, cd* f2)
 {
@@ -132,6 +169,14 @@ __device__ void radial(cd k, double rhom, double d, double Rmax, cd* f1, cd* f2)
         }
         *f1 = s1 * (Rmax * Rmax);
         *f2 = s2;
+        return;
+    }
+    if (d == 0.0) {
+        // coplanar point: closed forms with z = j k rhom
+        cd z = mk(-k.im * rhom, k.re * rhom), e = cexpc(mk(-z.re, -z.im));
+        cd jk = mk(-k.im, k.re);
+        *f1 = cdivc(mk(1, 0) - e * (mk(1, 0) + z), jk * jk);
+        *f2 = mk(1, 0) - e - ein(z);
         return;
     }
     // beyond R = RCUT/|Im k| the exponential is below 1e-15: f1 has no
@@ -172,9 +217,18 @@ __device__ void inner_polar(v3 r, v3 v0, v3 v1, v3 v2, cd k, Inner& o)
     v3 vv[3] = {v0, v1, v2};
     v3 nm = cross(v1 - v0, v2 - v0);
     nm = (1.0 / nrm(nm)) * nm;
-    double dd = dot(r - v0, nm), ad = fabs(dd);
+    double dd = dot(r - v0, nm);
     v3 rho0 = r - dd * nm;
     double Rmax = fmax(nrm(v0 - r), fmax(nrm(v1 - r), nrm(v2 - r)));
+    if (fabs(dd) < 1e-12 * Rmax) dd = 0.0;  // on the plane up to rounding
+    double ad = fabs(dd);
+    o.Is = mk(0, 0);
+    for (int d = 0; d < 3; d++) o.Iv[d] = o.Ig[d] = mk(0, 0);
+    if (k.im != 0.0) {  // whole triangle beyond RCUT/|Im k|: every term below exp(-RCUT)
+        v3 c = (1.0 / 3.0) * (v0 + v1 + v2);
+        double rc = fmax(nrm(v0 - c), fmax(nrm(v1 - c), nrm(v2 - c)));
+        if (nrm(r - c) - rc > RCUT / fabs(k.im)) return;
+    }
     cd Is = mk(0, 0), Ign = mk(0, 0), Iv[3] = {mk(0, 0), mk(0, 0), mk(0, 0)}, Igt[3] = {mk(0, 0), mk(0, 0), mk(0, 0)};
     double Omega = 0.0;
     cd mjk = mk(k.im, -k.re);  // -j k
@@ -427,8 +481,9 @@ __global__ void k_lagtab(int Lm, double h, double kr, double ki, double2* __rest
 }
 
 // Per pair: exact local entries (LA 3x3, K 3x3, Lphi) minus the grid's own
-// entries for the pair when the operator has a grid.  One warp per pair;
-// lanes own the test-stencil nodes u.  out: 19 complex per pair.
+// entries for the pair when the operator has a grid, plus the exact LA and
+// Lphi.  One warp per pair; lanes own the test-stencil nodes u.  out: NLOC
+// complex per pair.
 __global__ void __launch_bounds__(128) k_near_local(const int32_t* __restrict__ pairs, int64_t np, DevMesh M,
                                                     const double2* __restrict__ mom, int has_grid, int S, int Mord,
                                                     const int32_t* __restrict__ base, const double* __restrict__ Wt,
@@ -504,7 +559,7 @@ __global__ void __launch_bounds__(128) k_near_local(const int32_t* __restrict__ 
     cd Q3 = mk(mm[7].x, mm[7].y);
     v3 ctc = ld3(M.cen + 3 * t);
     double At = M.area[t], As = M.area[s];
-    double2* o = out + 19 * p;
+    double2* o = out + NLOC * p;
     for (int i = 0; i < 3; i++) {
         double cm = M.coef[3 * t + i];
         v3 pm = ld3(M.V + 3 * M.T[3 * t + i]) - ctc;
@@ -515,7 +570,9 @@ __global__ void __launch_bounds__(128) k_near_local(const int32_t* __restrict__ 
                     dot(pm, pn) * Q0;
             v3 dl = pn - pm, cx = cross(pn, pm);
             cd kk = dl.x * U[0] + dl.y * U[1] + dl.z * U[2] + cx.x * Vv[0] + cx.y * Vv[1] + cx.z * Vv[2];
-            la = (cm * cn) * la - gLA[3 * i + j];
+            la = (cm * cn) * la;
+            o[19 + 3 * i + j] = make_double2(la.re, la.im);  // exact
+            la = la - gLA[3 * i + j];
             kk = (cm * cn) * kk - gK[3 * i + j];
             o[3 * i + j] = make_double2(la.re, la.im);
             o[9 + 3 * i + j] = make_double2(kk.re, kk.im);
@@ -523,14 +580,19 @@ __global__ void __launch_bounds__(128) k_near_local(const int32_t* __restrict__ 
     }
     cd lp = (1.0 / (At * As)) * (Q0 - g0);
     o[18] = make_double2(lp.re, lp.im);
+    cd lpe = (1.0 / (At * As)) * Q0;
+    o[28] = make_double2(lpe.re, lpe.im);  // exact
 }
 
 // CSR values: entry (m, n) sums the local entries of the near pairs (t, s)
 // with t in supp(f_m), s in supp(f_n), in a fixed order (deterministic).
+// vL = L (exact - grid), vK = K (exact - grid), vLA = LA (exact - grid);
+// diagonal entries also give the exact LA and L diagonals (dLA, dL).
 __global__ void k_csr_fill(int ne, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                            const int64_t* __restrict__ pstart, const int32_t* __restrict__ pairs,
                            const double2* __restrict__ loc, DevMesh M, double2 invk2, double2* __restrict__ vL,
-                           double2* __restrict__ vK)
+                           double2* __restrict__ vK, double2* __restrict__ vLA, double2* __restrict__ dLA,
+                           double2* __restrict__ dL)
 {
     int m = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
@@ -538,7 +600,7 @@ __global__ void k_csr_fill(int ne, const int64_t* __restrict__ row_ptr, const in
     cd ik2 = mk(invk2.x, invk2.y);
     for (int64_t e = row_ptr[m] + lane; e < row_ptr[m + 1]; e += 32) {
         int n = col[e];
-        cd L = mk(0, 0), K = mk(0, 0);
+        cd L = mk(0, 0), K = mk(0, 0), LA = mk(0, 0), LAx = mk(0, 0), Lx = mk(0, 0);
         for (int a = 0; a < 2; a++) {
             int t = M.edge_tri[2 * m + a], i = M.edge_slot[2 * m + a];
             int64_t lo = pstart[t], hi = pstart[t + 1];
@@ -554,16 +616,35 @@ __global__ void k_csr_fill(int ne, const int64_t* __restrict__ row_ptr, const in
                         r = mid;
                 }
                 if (l < hi && pairs[2 * l + 1] == s) {
-                    const double2* o = loc + 19 * l;
+                    const double2* o = loc + NLOC * l;
                     double c4 = 4.0 * M.coef[3 * t + i] * M.coef[3 * s + j] * M.area[t] * M.area[s];
-                    cd lp = mk(o[18].x, o[18].y);
-                    L = L + mk(o[3 * i + j].x, o[3 * i + j].y) - c4 * (ik2 * lp);
+                    cd lp = mk(o[18].x, o[18].y), lpe = mk(o[28].x, o[28].y);
+                    cd la = mk(o[3 * i + j].x, o[3 * i + j].y), lae = mk(o[19 + 3 * i + j].x, o[19 + 3 * i + j].y);
+                    LA = LA + la;
+                    L = L + la - c4 * (ik2 * lp);
                     K = K + mk(o[9 + 3 * i + j].x, o[9 + 3 * i + j].y);
+                    LAx = LAx + lae;
+                    Lx = Lx + lae - c4 * (ik2 * lpe);
                 }
             }
         }
         vL[e] = make_double2(L.re, L.im);
         vK[e] = make_double2(K.re, K.im);
+        vLA[e] = make_double2(LA.re, LA.im);
+        if (n == m) {
+            dLA[m] = make_double2(LAx.re, LAx.im);
+            dL[m] = make_double2(Lx.re, Lx.im);
+        }
+    }
+}
+
+__global__ void k_lphi_vals(int64_t np, const double2* __restrict__ loc, double2* __restrict__ v,
+                            double2* __restrict__ vnr)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) {
+        v[p] = loc[NLOC * p + 18];    // exact - grid
+        vnr[p] = loc[NLOC * p + 28];  // exact (near-region matrix, preconditioner)
     }
 }
 
@@ -578,7 +659,7 @@ sie_status near_build(sie_op* op, AimOp& a, const QuadDev& q)
     SIE_CUDA_TRY(cudaMemcpyAsync(a.pairs, a.hpairs.data(), sizeof(int32_t) * 2 * a.npairs, cudaMemcpyHostToDevice, st));
     double2 *mom = nullptr, *loc = nullptr, *tab = nullptr;
     SIE_CUDA_TRY(cudaMallocAsync((void**)&mom, sizeof(double2) * 14 * std::max<int64_t>(a.npairs, 1), st));
-    SIE_CUDA_TRY(cudaMallocAsync((void**)&loc, sizeof(double2) * 19 * std::max<int64_t>(a.npairs, 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&loc, sizeof(double2) * NLOC * std::max<int64_t>(a.npairs, 1), st));
     const int wpb = 4;
     if (a.npairs > 0) {
         k_near_moments<<<(unsigned)((a.npairs + wpb - 1) / wpb), 32 * wpb, 0, st>>>(a.pairs, a.npairs, M, a.kr, a.ki,
@@ -611,13 +692,34 @@ sie_status near_build(sie_op* op, AimOp& a, const QuadDev& q)
     SIE_CUDA_TRY(cudaMallocAsync((void**)&a.col, sizeof(int32_t) * std::max<int64_t>(a.nnz, 1), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&a.valL, sizeof(double2) * std::max<int64_t>(a.nnz, 1), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&a.valK, sizeof(double2) * std::max<int64_t>(a.nnz, 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&a.valLA, sizeof(double2) * std::max<int64_t>(a.nnz, 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&a.dLA, sizeof(double2) * H.ne, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&a.dL, sizeof(double2) * H.ne, st));
+    SIE_CUDA_TRY(cudaMemsetAsync(a.dLA, 0, sizeof(double2) * H.ne, st));
+    SIE_CUDA_TRY(cudaMemsetAsync(a.dL, 0, sizeof(double2) * H.ne, st));
     SIE_CUDA_TRY(cudaMemcpyAsync(a.row_ptr, a.csr.row_ptr.data(), sizeof(int64_t) * (H.ne + 1), cudaMemcpyHostToDevice, st));
     SIE_CUDA_TRY(cudaMemcpyAsync(a.col, a.csr.col.data(), sizeof(int32_t) * a.nnz, cudaMemcpyHostToDevice, st));
     std::complex<double> kk(a.kr, a.ki);
     std::complex<double> ik2 = 1.0 / (kk * kk);
     k_csr_fill<<<(unsigned)((H.ne + 3) / 4), 128, 0, st>>>((int)H.ne, a.row_ptr, a.col, dps, a.pairs, loc, M,
-                                                           make_double2(ik2.real(), ik2.imag()), a.valL, a.valK);
+                                                           make_double2(ik2.real(), ik2.imag()), a.valL, a.valK,
+                                                           a.valLA, a.dLA, a.dL);
     SIE_CUDA_TRY(cudaGetLastError());
+    // triangle CSR of Lphi (exact - grid): rows = pair blocks, columns = s
+    a.tri_row_ptr_h = pstart;
+    a.tri_col_h.resize(a.npairs);
+    for (int64_t p = 0; p < a.npairs; p++) a.tri_col_h[p] = a.hpairs[2 * p + 1];
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&a.tri_row_ptr, sizeof(int64_t) * (H.nt + 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&a.tri_col, sizeof(int32_t) * std::max<int64_t>(a.npairs, 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&a.valLphi, sizeof(double2) * std::max<int64_t>(a.npairs, 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&a.valLphiNR, sizeof(double2) * std::max<int64_t>(a.npairs, 1), st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(a.tri_row_ptr, a.tri_row_ptr_h.data(), sizeof(int64_t) * (H.nt + 1),
+                                 cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(a.tri_col, a.tri_col_h.data(), sizeof(int32_t) * a.npairs, cudaMemcpyHostToDevice, st));
+    if (a.npairs > 0) {
+        k_lphi_vals<<<(unsigned)((a.npairs + 255) / 256), 256, 0, st>>>(a.npairs, loc, a.valLphi, a.valLphiNR);
+        SIE_CUDA_TRY(cudaGetLastError());
+    }
     SIE_CUDA_TRY(cudaFreeAsync(dps, st));
     SIE_CUDA_TRY(cudaFreeAsync(mom, st));
     SIE_CUDA_TRY(cudaFreeAsync(loc, st));

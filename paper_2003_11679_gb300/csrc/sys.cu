@@ -1,0 +1,829 @@
+// GIBC system of Eq. (sys) on the GPU: the augmented exterior product
+// [j k0 LA - (K_0 + Ix/2) Z', D^T Lphi B; F D, j k0 I] [H; c0 rho] with the AIM
+// grid carrying all seven source grids at once (7 forward, 4 inverse FFTs),
+// the interior impedance Z' = Z_i / eta0 of Eqs. (GIBCdef), (nest02), (nest2)
+// applied by a nested Krylov solve, restarted flexible GMRES with FP64
+// classical Gram-Schmidt (twice), plane-wave right-hand sides and the far
+// field / RCS of the solution.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <functional>
+#include <vector>
+
+#include "internal.h"
+
+namespace sie {
+
+using cplx = std::complex<double>;
+static const double C0 = 299792458.0, MU0 = 4e-7 * M_PI, ETA0 = MU0 * C0;
+
+// ------------------------------------------------------------------ vector kernels
+__global__ void k_axpby(int64_t n, double2 a, const double2* __restrict__ x, double2 b, double2* __restrict__ y)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 xv = x[i];
+    double2 o = make_double2(a.x * xv.x - a.y * xv.y, a.x * xv.y + a.y * xv.x);
+    if (b.x != 0.0 || b.y != 0.0) {  // y is not read when b = 0 (may be uninitialised)
+        double2 yv = y[i];
+        o.x += b.x * yv.x - b.y * yv.y;
+        o.y += b.x * yv.y + b.y * yv.x;
+    }
+    y[i] = o;
+}
+
+// y[i] = x[i] / (s d[i]) (Jacobi) ; d == null -> y = x / s
+__global__ void k_jacobi(int64_t n, const double2* __restrict__ x, const double2* __restrict__ d, double2 s,
+                         double2* __restrict__ y)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 dv = d ? d[i] : make_double2(1.0, 0.0);
+    double2 q = make_double2(s.x * dv.x - s.y * dv.y, s.x * dv.y + s.y * dv.x);
+    double den = q.x * q.x + q.y * q.y;
+    double2 xv = x[i];
+    y[i] = make_double2((xv.x * q.x + xv.y * q.y) / den, (xv.y * q.x - xv.x * q.y) / den);
+}
+
+// out[j] = sum_k conj(V[j][k]) w[k], one block per basis vector (fixed-order tree)
+__global__ void __launch_bounds__(256) k_dots(int64_t n, const double2* __restrict__ V, int64_t ld,
+                                              const double2* __restrict__ w, double2* __restrict__ out)
+{
+    const double2* v = V + (int64_t)blockIdx.x * ld;
+    double sr = 0, si = 0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        double2 a = v[k], b = w[k];
+        sr += a.x * b.x + a.y * b.y;
+        si += a.x * b.y - a.y * b.x;
+    }
+    __shared__ double rr[256], ri[256];
+    rr[threadIdx.x] = sr;
+    ri[threadIdx.x] = si;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            rr[threadIdx.x] += rr[threadIdx.x + s];
+            ri[threadIdx.x] += ri[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = make_double2(rr[0], ri[0]);
+}
+
+// w -= sum_j V[j] h[j]   (sgn = -1) or x += sum_j V[j] h[j] (sgn = +1)
+__global__ void k_gemv(int64_t n, int nv, const double2* __restrict__ V, int64_t ld, const double2* __restrict__ h,
+                       double sgn, double2* __restrict__ w)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double sr = 0, si = 0;
+    for (int j = 0; j < nv; j++) {
+        double2 a = V[(int64_t)j * ld + k], b = h[j];
+        sr += a.x * b.x - a.y * b.y;
+        si += a.x * b.y + a.y * b.x;
+    }
+    double2 o = w[k];
+    w[k] = make_double2(o.x + sgn * sr, o.y + sgn * si);
+}
+
+static unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+static sie_status axpby(cudaStream_t st, int64_t n, cplx a, const double2* x, cplx b, double2* y)
+{
+    k_axpby<<<nb(n), 256, 0, st>>>(n, make_double2(a.real(), a.imag()), x, make_double2(b.real(), b.imag()), y);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+// ------------------------------------------------------------------ FGMRES
+using Apply = std::function<sie_status(const double2*, double2*)>;
+
+sie_status KrylovWork::alloc(cudaStream_t st, int64_t n_, int m_)
+{
+    if (n_ == n && m_ == m) return SIE_OK;
+    release(st);
+    n = n_;
+    m = m_;
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&V, sizeof(double2) * (m + 1) * n, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&Z, sizeof(double2) * m * n, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&w, sizeof(double2) * n, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&r, sizeof(double2) * n, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&h, sizeof(double2) * 2 * (m + 1), st));
+    return SIE_OK;
+}
+
+void KrylovWork::release(cudaStream_t st)
+{
+    for (double2* p : {V, Z, w, h, r})
+        if (p) cudaFreeAsync(p, st);
+    V = Z = w = h = r = nullptr;
+    n = 0;
+    m = 0;
+}
+
+static sie_status dev_norm(cudaStream_t st, int64_t n, const double2* x, double2* tmp, double* out)
+{
+    k_dots<<<1, 256, 0, st>>>(n, x, n, x, tmp);
+    SIE_CUDA_TRY(cudaGetLastError());
+    double2 v;
+    SIE_CUDA_TRY(cudaMemcpyAsync(&v, tmp, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = std::sqrt(std::max(v.x, 0.0));
+    return SIE_OK;
+}
+
+// Right-preconditioned restarted flexible GMRES, zero initial guess; the
+// monitored residual is the true residual of A x = b.  Arnoldi in FP64 with
+// classical Gram-Schmidt applied twice.
+static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, const Apply& Minv, const double2* b,
+                         double2* x, double tol, int maxit, int restart, int* iters_out, double* relres_out)
+{
+    cudaStream_t st = c->stream;
+    SIE_TRY(K.alloc(st, n, restart));
+    SIE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
+    double bnorm;
+    SIE_TRY(dev_norm(st, n, b, K.h, &bnorm));
+    int it = 0;
+    double rel = 1.0;
+    if (bnorm == 0.0) {
+        if (iters_out) *iters_out = 0;
+        if (relres_out) *relres_out = 0.0;
+        return SIE_OK;
+    }
+    SIE_CUDA_TRY(cudaMemcpyAsync(K.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+    double beta = bnorm;
+    std::vector<cplx> H((restart + 1) * restart), g(restart + 1), cs(restart), sn(restart), hv(restart + 1),
+        h2(restart + 1);
+    while (true) {
+        SIE_TRY(axpby(st, n, cplx(1.0 / beta, 0), K.r, 0.0, K.V));
+        std::fill(g.begin(), g.end(), cplx(0));
+        g[0] = beta;
+        int j = 0, jend = -1;
+        for (; j < restart; j++) {
+            double2* Vj = K.V + (int64_t)j * n;
+            double2* Zj = K.Z + (int64_t)j * n;
+            SIE_TRY(Minv(Vj, Zj));
+            SIE_TRY(A(Zj, K.w));
+            // CGS2
+            for (int pass = 0; pass < 2; pass++) {
+                k_dots<<<j + 1, 256, 0, st>>>(n, K.V, n, K.w, K.h);
+                SIE_CUDA_TRY(cudaGetLastError());
+                k_gemv<<<nb(n), 256, 0, st>>>(n, j + 1, K.V, n, K.h, -1.0, K.w);
+                SIE_CUDA_TRY(cudaGetLastError());
+                SIE_CUDA_TRY(cudaMemcpyAsync(pass ? h2.data() : hv.data(), K.h, sizeof(double2) * (j + 1),
+                                             cudaMemcpyDeviceToHost, st));
+            }
+            double hn;
+            SIE_TRY(dev_norm(st, n, K.w, K.h + restart + 1, &hn));  // syncs: hv, h2 valid
+            for (int i = 0; i <= j; i++) H[i * restart + j] = hv[i] + h2[i];
+            H[(j + 1) * restart + j] = hn;
+            if (hn > 0) SIE_TRY(axpby(st, n, cplx(1.0 / hn, 0), K.w, 0.0, K.V + (int64_t)(j + 1) * n));
+            // previous rotations
+            for (int i = 0; i < j; i++) {
+                cplx a = H[i * restart + j], bb = H[(i + 1) * restart + j];
+                H[i * restart + j] = cs[i] * a + sn[i] * bb;
+                H[(i + 1) * restart + j] = -std::conj(sn[i]) * a + cs[i] * bb;
+            }
+            cplx a = H[j * restart + j], bb = H[(j + 1) * restart + j];
+            double den = std::sqrt(std::norm(a) + std::norm(bb));
+            if (std::abs(a) == 0.0) {
+                cs[j] = 0.0;
+                sn[j] = 1.0;
+            } else {
+                cs[j] = std::abs(a) / den;
+                sn[j] = (a / std::abs(a)) * std::conj(bb) / den;
+            }
+            H[j * restart + j] = cs[j] * a + sn[j] * bb;
+            H[(j + 1) * restart + j] = 0.0;
+            cplx gj = g[j];
+            g[j] = cs[j] * gj;
+            g[j + 1] = -std::conj(sn[j]) * gj;
+            it++;
+            rel = std::abs(g[j + 1]) / bnorm;
+            if (rel < tol || it >= maxit || hn == 0.0) {
+                jend = j;
+                break;
+            }
+        }
+        if (jend < 0) jend = restart - 1;
+        // back substitution
+        std::vector<cplx> y(jend + 1);
+        for (int i = jend; i >= 0; i--) {
+            cplx s = g[i];
+            for (int k2 = i + 1; k2 <= jend; k2++) s -= H[i * restart + k2] * y[k2];
+            y[i] = s / H[i * restart + i];
+        }
+        std::vector<double2> yd(jend + 1);
+        for (int i = 0; i <= jend; i++) yd[i] = make_double2(y[i].real(), y[i].imag());
+        SIE_CUDA_TRY(cudaMemcpyAsync(K.h, yd.data(), sizeof(double2) * (jend + 1), cudaMemcpyHostToDevice, st));
+        k_gemv<<<nb(n), 256, 0, st>>>(n, jend + 1, K.Z, n, K.h, 1.0, x);
+        SIE_CUDA_TRY(cudaGetLastError());
+        SIE_CUDA_TRY(cudaStreamSynchronize(st));  // yd (pageable) consumed
+        if (rel < tol || it >= maxit) break;
+        // true residual for the restart
+        SIE_TRY(A(x, K.w));
+        SIE_CUDA_TRY(cudaMemcpyAsync(K.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+        SIE_TRY(axpby(st, n, -1.0, K.w, 1.0, K.r));
+        SIE_TRY(dev_norm(st, n, K.r, K.h, &beta));
+        rel = beta / bnorm;
+        if (rel < tol) break;
+    }
+    if (iters_out) *iters_out = it;
+    if (relres_out) *relres_out = rel;
+    return rel < tol ? SIE_OK : SIE_ERR_NOT_CONVERGED;
+}
+
+// ------------------------------------------------------------------ system kernels
+// grids: J from H (0..2), M from E' (3..5), charge grid from q_t = -c0rho_t (6)
+__global__ void k_project_sys(int nt, int S, int Mord, DevMesh M, const int32_t* __restrict__ base,
+                              const double* __restrict__ W, const double2* __restrict__ H,
+                              const double2* __restrict__ E, const double2* __restrict__ rho, GridDesc g,
+                              double2* __restrict__ src, int64_t Ng)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nt * S) return;
+    int t = idx / S, u = idx % S;
+    const int Mp = Mord + 1;
+    int nx = base[3 * t] + u % Mp, ny = base[3 * t + 1] + (u / Mp) % Mp, nz = base[3 * t + 2] + u / (Mp * Mp);
+    int64_t node = ((int64_t)nz * g.N[1] + ny) * g.N[0] + nx;
+    const double* w = W + (size_t)idx * 4;
+    for (int f = 0; f < 2; f++) {
+        const double2* x = f ? E : H;
+        double2 al = make_double2(0, 0);
+        double2 be[3] = {al, al, al};
+        for (int i = 0; i < 3; i++) {
+            double2 xv = x[M.tri_edge[3 * t + i]];
+            double c = M.coef[3 * t + i];
+            al.x += c * xv.x;
+            al.y += c * xv.y;
+            for (int a = 0; a < 3; a++) {
+                double qq = c * M.q[9 * t + 3 * i + a];
+                be[a].x += qq * xv.x;
+                be[a].y += qq * xv.y;
+            }
+        }
+        for (int a = 0; a < 3; a++) {
+            double2* d = src + (3 * f + a) * Ng + node;
+            atomicAdd(&d->x, al.x * w[1 + a] + be[a].x * w[0]);
+            atomicAdd(&d->y, al.y * w[1 + a] + be[a].y * w[0]);
+        }
+    }
+    double2 r = rho[t];
+    double2* d = src + 6 * Ng + node;
+    atomicAdd(&d->x, -r.x * w[0]);
+    atomicAdd(&d->y, -r.y * w[0]);
+}
+
+// A_a = j k0 G J_a - (Ggrad x M)_a into grids 0..2, Phi = G rho into grid 3
+__global__ void k_specmul_sys(const double2* __restrict__ spec, double2* __restrict__ buf, int64_t nn, double k0)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    auto mul = [](double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
+    double2 G = spec[i], gx = spec[nn + i], gy = spec[2 * nn + i], gz = spec[3 * nn + i];
+    double2 jG = make_double2(-k0 * G.y, k0 * G.x);  // j k0 G
+    double2 mx = buf[3 * nn + i], my = buf[4 * nn + i], mz = buf[5 * nn + i];
+    double2 cx = mul(gy, mz), cy = mul(gz, mx), cz = mul(gx, my);
+    double2 dx = mul(gz, my), dy = mul(gx, mz), dz = mul(gy, mx);
+    double2 a0 = mul(jG, buf[i]), a1 = mul(jG, buf[nn + i]), a2 = mul(jG, buf[2 * nn + i]);
+    buf[i] = make_double2(a0.x - (cx.x - dx.x), a0.y - (cx.y - dx.y));
+    buf[nn + i] = make_double2(a1.x - (cy.x - dy.x), a1.y - (cy.y - dy.y));
+    buf[2 * nn + i] = make_double2(a2.x - (cz.x - dz.x), a2.y - (cz.y - dz.y));
+    buf[3 * nn + i] = mul(G, buf[6 * nn + i]);
+}
+
+// y[r] += alpha * sum_e val[e] x[col[e]]
+__global__ void k_spmv_a(int nrow, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                         const double2* __restrict__ val, const double2* __restrict__ x, double2 alpha,
+                         double2* __restrict__ y)
+{
+    int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x & 31;
+    if (r >= nrow) return;
+    double ar = 0, ai = 0;
+    for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += 32) {
+        double2 v = val[e], xv = x[col[e]];
+        ar += v.x * xv.x - v.y * xv.y;
+        ai += v.x * xv.y + v.y * xv.x;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        ar += __shfl_down_sync(0xffffffffu, ar, off);
+        ai += __shfl_down_sync(0xffffffffu, ai, off);
+    }
+    if (lane == 0) {
+        y[r].x += alpha.x * ar - alpha.y * ai;
+        y[r].y += alpha.x * ai + alpha.y * ar;
+    }
+}
+
+static sie_status spmv(cudaStream_t st, int nrow, const int64_t* rp, const int32_t* col, const double2* val,
+                       const double2* x, cplx alpha, double2* y)
+{
+    k_spmv_a<<<(nrow + 3) / 4, 128, 0, st>>>(nrow, rp, col, val, x, make_double2(alpha.real(), alpha.imag()), y);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+// sigma_t = -A_t c0rho_t
+__global__ void k_sigma(int nt, const double* __restrict__ area, const double2* __restrict__ rho,
+                        double2* __restrict__ sig)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nt) sig[t] = make_double2(-area[t] * rho[t].x, -area[t] * rho[t].y);
+}
+
+__global__ void k_fdiv_area(int nt, const double* __restrict__ area, double2* __restrict__ x)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nt) x[t] = make_double2(x[t].x / area[t], x[t].y / area[t]);
+}
+
+// y1_m += l_m (phi_{T+} - phi_{T-}) = (D^T phi)_m
+__global__ void k_dt(int ne, const int32_t* __restrict__ edge_tri, const double* __restrict__ len,
+                     const double2* __restrict__ phi, double2* __restrict__ y)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= ne) return;
+    double2 a = phi[edge_tri[2 * m]], b = phi[edge_tri[2 * m + 1]];
+    y[m].x += len[m] * (a.x - b.x);
+    y[m].y += len[m] * (a.y - b.y);
+}
+
+// q_t = (D y)_t / A_t * scaleA  -> with scaleA = A_t gives (D y)_t; here
+// (D y)_t = sum_i s_i l_i y_e = 2 A_t sum_i c_{t,i} y_{e(t,i)}
+__global__ void k_D(int nt, DevMesh M, const double2* __restrict__ y, double2* __restrict__ q)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double sr = 0, si = 0;
+    for (int i = 0; i < 3; i++) {
+        double2 v = y[M.tri_edge[3 * t + i]];
+        double c = 2.0 * M.coef[3 * t + i] * M.area[t];
+        sr += c * v.x;
+        si += c * v.y;
+    }
+    q[t] = make_double2(sr, si);
+}
+
+// row 2: y2_t = (F D H)_t + j k0 c0rho_t = 2 sum_i c_{t,i} H_{e(t,i)} + j k0 c0rho_t
+__global__ void k_row2(int nt, DevMesh M, const double2* __restrict__ H, const double2* __restrict__ rho, double k0,
+                       double2* __restrict__ y2)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double sr = 0, si = 0;
+    for (int i = 0; i < 3; i++) {
+        double2 h = H[M.tri_edge[3 * t + i]];
+        double c = 2.0 * M.coef[3 * t + i];
+        sr += c * h.x;
+        si += c * h.y;
+    }
+    double2 r = rho[t];
+    y2[t] = make_double2(sr - k0 * r.y, si + k0 * r.x);
+}
+
+// plane-wave right-hand side b_m = -(1/eta0) I f_m . e exp(-j k0 khat . r)
+struct GL8 {
+    double x[16], w[16];
+    int n;
+};
+
+__global__ void k_rhs(int nt, DevMesh M, GL8 q, double k0, double3 kh, double3 ep, double scale,
+                      double2* __restrict__ b)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const double* a = M.V + 3 * M.T[3 * t];
+    const double* bb = M.V + 3 * M.T[3 * t + 1];
+    const double* c = M.V + 3 * M.T[3 * t + 2];
+    double e1[3], e2[3];
+    for (int d = 0; d < 3; d++) {
+        e1[d] = bb[d] - a[d];
+        e2[d] = c[d] - a[d];
+    }
+    double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2], nz = e1[0] * e2[1] - e1[1] * e2[0];
+    double twoA = sqrt(nx * nx + ny * ny + nz * nz);
+    double accr[3] = {0, 0, 0}, acci[3] = {0, 0, 0};
+    for (int i = 0; i < q.n; i++) {
+        double u = q.x[i];
+        for (int j = 0; j < q.n; j++) {
+            double v = q.x[j] * (1.0 - u);
+            double w = twoA * (1.0 - u) * q.w[i] * q.w[j];
+            double r[3];
+            for (int d = 0; d < 3; d++) r[d] = a[d] + u * e1[d] + v * e2[d];
+            double ph = -k0 * (kh.x * r[0] + kh.y * r[1] + kh.z * r[2]);
+            double s, cc;
+            sincos(ph, &s, &cc);
+            for (int sl = 0; sl < 3; sl++) {
+                const double* p = M.V + 3 * M.T[3 * t + sl];
+                double f = M.coef[3 * t + sl] * ((r[0] - p[0]) * ep.x + (r[1] - p[1]) * ep.y + (r[2] - p[2]) * ep.z);
+                accr[sl] += w * f * cc;
+                acci[sl] += w * f * s;
+            }
+        }
+    }
+    for (int sl = 0; sl < 3; sl++) {
+        double2* d = b + M.tri_edge[3 * t + sl];
+        atomicAdd(&d->x, scale * accr[sl]);
+        atomicAdd(&d->y, scale * acci[sl]);
+    }
+}
+
+// far-field sums N(X)_a = sum_n X_n I f_n,a exp(j k0 rhat . r) for X = H, E';
+// one block per direction, fixed-order tree reduction; out: 6 complex per dir
+__global__ void __launch_bounds__(256) k_far(int nt, DevMesh M, GL8 q, double k0, const double* __restrict__ rhat,
+                                             const double2* __restrict__ H, const double2* __restrict__ E,
+                                             double2* __restrict__ out)
+{
+    int d = blockIdx.x;
+    double rx = rhat[3 * d], ry = rhat[3 * d + 1], rz = rhat[3 * d + 2];
+    double acc[12];
+    for (int i = 0; i < 12; i++) acc[i] = 0;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const double* a = M.V + 3 * M.T[3 * t];
+        const double* bb = M.V + 3 * M.T[3 * t + 1];
+        const double* c = M.V + 3 * M.T[3 * t + 2];
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; k++) {
+            e1[k] = bb[k] - a[k];
+            e2[k] = c[k] - a[k];
+        }
+        double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2],
+               nz = e1[0] * e2[1] - e1[1] * e2[0];
+        double twoA = sqrt(nx * nx + ny * ny + nz * nz);
+        for (int i = 0; i < q.n; i++) {
+            double u = q.x[i];
+            for (int j = 0; j < q.n; j++) {
+                double v = q.x[j] * (1.0 - u);
+                double w = twoA * (1.0 - u) * q.w[i] * q.w[j];
+                double r[3];
+                for (int k = 0; k < 3; k++) r[k] = a[k] + u * e1[k] + v * e2[k];
+                double s, cc;
+                sincos(k0 * (rx * r[0] + ry * r[1] + rz * r[2]), &s, &cc);
+                for (int sl = 0; sl < 3; sl++) {
+                    const double* p = M.V + 3 * M.T[3 * t + sl];
+                    int e = M.tri_edge[3 * t + sl];
+                    double cf = w * M.coef[3 * t + sl];
+                    double2 h = H[e], ev = E[e];
+                    for (int k = 0; k < 3; k++) {
+                        double f = cf * (r[k] - p[k]);
+                        // x * exp(j phase)
+                        acc[2 * k] += f * (h.x * cc - h.y * s);
+                        acc[2 * k + 1] += f * (h.x * s + h.y * cc);
+                        acc[6 + 2 * k] += f * (ev.x * cc - ev.y * s);
+                        acc[6 + 2 * k + 1] += f * (ev.x * s + ev.y * cc);
+                    }
+                }
+            }
+        }
+    }
+    __shared__ double red[256];
+    for (int i = 0; i < 12; i++) {
+        red[threadIdx.x] = acc[i];
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) ((double*)(out + 6 * d))[i] = red[0];
+        __syncthreads();
+    }
+}
+
+static GL8 gl_rule(int n)
+{
+    GL8 q;
+    q.n = n;
+    gauss_legendre01(n, q.x, q.w);
+    return q;
+}
+
+// ------------------------------------------------------------------ operators
+static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork& K, const double2* v, double2* y);
+
+// interior impedance E' = Z' H = -(j k0 eps_r + sigma eta0)^-1 L_i^-1 (K_i - Ix/2) H
+static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_iters)
+{
+    sie_ctx* c = op->mesh->ctx;
+    cudaStream_t st = c->stream;
+    const int64_t ne = op->mesh->h.ne;
+    double2* a = op->sys_tmp;  // ne
+    SIE_TRY(aim_apply(op, op->inn, 1, H, a));
+    SIE_TRY(spmv(st, (int)ne, op->ix_row_ptr, op->ix_col, op->ix_val, H, cplx(-0.5, 0), a));
+    AimOp& I = op->inn;
+    Apply A = [&](const double2* x, double2* y) { return aim_apply(op, I, 0, x, y); };
+    cplx ki(I.kr, I.ki);
+    Apply Minv = [&](const double2* x, double2* y) { return constraint_solve(op, I, 1.0 / (ki * ki), op->kcs_in, x, y); };
+    int it = 0;
+    double rr = 0;
+    sie_status s;
+    {
+        Stage s_(c, "inner_solve");
+        s = fgmres(c, op->kin, ne, A, Minv, a, E, op->p.tol_inner, op->p.inner_maxit, std::min(op->p.restart, 60),
+                   &it, &rr);
+    }
+    if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
+    if (inner_iters) *inner_iters = it;
+    op->stats[2] = std::max(op->stats[2], (double)it);
+    op->stats[3] = std::max(op->stats[3], rr);
+    cplx zs(0.0, op->k0 * op->eps_r);
+    zs += op->sigma * ETA0;
+    SIE_TRY(axpby(st, ne, -1.0 / zs, E, 0.0, E));
+    return SIE_OK;
+}
+
+// y = SYS x, x = [H (ne); c0 rho (nt)]
+static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
+{
+    sie_ctx* c = op->mesh->ctx;
+    cudaStream_t st = c->stream;
+    const DevMesh& M = op->mesh->d;
+    const int64_t ne = M.ne, nt = M.nt;
+    const double2* H = x;
+    const double2* rho = x + ne;
+    double2* y1 = y;
+    double2* y2 = y + ne;
+    double2* E = op->sys_E;
+    SIE_TRY(apply_Z(op, H, E, nullptr));
+    AimOp& X = op->ext;
+    const GridDesc& g = X.g;
+    int S = (g.M + 1) * (g.M + 1) * (g.M + 1);
+    int64_t Ng = (int64_t)g.N[0] * g.N[1] * g.N[2];
+    int64_t nn = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    double2* src = op->ws.src;
+    double2* buf = op->ws.bufs;
+    {
+        Stage s_(c, "project_sys");
+        SIE_CUDA_TRY(cudaMemsetAsync(src, 0, sizeof(double2) * 7 * Ng, st));
+        k_project_sys<<<(unsigned)((M.nt * S + 255) / 256), 256, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, H, E, rho,
+                                                                           g, src, Ng);
+        SIE_CUDA_TRY(cudaGetLastError());
+    }
+    for (int k = 0; k < 7; k++) SIE_TRY(fft3d(st, buf + k * nn, src + k * Ng, g, -1, 1, c));
+    {
+        Stage s_(c, "specmul_sys");
+        k_specmul_sys<<<nb(nn), 256, 0, st>>>(X.spec, buf, nn, op->k0);
+        SIE_CUDA_TRY(cudaGetLastError());
+    }
+    for (int k = 0; k < 4; k++) SIE_TRY(fft3d(st, buf + k * nn, src + k * Ng, g, +1, 1, c));
+    SIE_CUDA_TRY(cudaMemsetAsync(y1, 0, sizeof(double2) * ne, st));
+    {
+        Stage s_(c, "interp");
+        SIE_TRY(aim_interp(op, src, 1, make_double2(1.0, 0.0), y1));
+    }
+    {
+        Stage s_(c, "spmv_sys");
+        SIE_TRY(spmv(st, (int)ne, X.row_ptr, X.col, X.valLA, H, cplx(0.0, op->k0), y1));
+        SIE_TRY(spmv(st, (int)ne, X.row_ptr, X.col, X.valK, E, cplx(-1.0, 0.0), y1));
+        SIE_TRY(spmv(st, (int)ne, op->ix_row_ptr, op->ix_col, op->ix_val, E, cplx(-0.5, 0.0), y1));
+        double2* sig = op->sys_tmp;
+        double2* phi = op->sys_tmp + nt;
+        k_sigma<<<nb(nt), 256, 0, st>>>((int)nt, M.area, rho, sig);
+        SIE_CUDA_TRY(cudaMemsetAsync(phi, 0, sizeof(double2) * nt, st));
+        SIE_TRY(spmv(st, (int)nt, X.tri_row_ptr, X.tri_col, X.valLphi, sig, cplx(1.0, 0.0), phi));
+        k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, phi, y1);
+        k_row2<<<nb(nt), 256, 0, st>>>((int)nt, M, H, rho, op->k0, y2);
+        SIE_CUDA_TRY(cudaGetLastError());
+    }
+    return SIE_OK;
+}
+
+// Constraint preconditioner (the near-region form of the AEFIE constraint
+// preconditioner of Sec. III-D): solves
+//     (Dg - kappa D^T Lphi_NR D) y = v
+// with Dg = diag(LA) (exact diagonal) and Lphi_NR the exact near-region
+// scalar-potential matrix, by block elimination on the charges q = D y:
+//     (I - kappa D Dg^-1 D^T Lphi_NR) q = D Dg^-1 v,   y = Dg^-1 (v + kappa D^T Lphi_NR q),
+// the triangle system solved by an inner GMRES to a loose tolerance (the
+// outer iterations are flexible).
+static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork& K, const double2* v, double2* y)
+{
+    sie_ctx* c = op->mesh->ctx;
+    cudaStream_t st = c->stream;
+    const DevMesh& M = op->mesh->d;
+    const int64_t ne = M.ne, nt = M.nt;
+    double2* t1 = op->cs_e;       // ne
+    double2* rq = op->cs_t;       // nt: right-hand side
+    double2* q = op->cs_t + nt;   // nt: solution
+    double2* ph = op->cs_t + 2 * nt;
+    double2* te = op->cs_e + ne;  // ne scratch
+    k_jacobi<<<nb(ne), 256, 0, st>>>(ne, v, a.dLA, make_double2(1.0, 0.0), t1);
+    k_D<<<nb(nt), 256, 0, st>>>((int)nt, M, t1, rq);
+    SIE_CUDA_TRY(cudaGetLastError());
+    Apply S = [&](const double2* x, double2* out) {
+        // out = x - kappa D Dg^-1 D^T Lphi x
+        SIE_CUDA_TRY(cudaMemsetAsync(ph, 0, sizeof(double2) * nt, st));
+        SIE_TRY(spmv(st, (int)nt, a.tri_row_ptr, a.tri_col, a.valLphiNR, x, 1.0, ph));
+        SIE_CUDA_TRY(cudaMemsetAsync(te, 0, sizeof(double2) * ne, st));
+        k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, ph, te);
+        k_jacobi<<<nb(ne), 256, 0, st>>>(ne, te, a.dLA, make_double2(1.0, 0.0), te);
+        k_D<<<nb(nt), 256, 0, st>>>((int)nt, M, te, out);
+        SIE_CUDA_TRY(cudaGetLastError());
+        return axpby(st, nt, 1.0, x, -kappa, out);
+    };
+    Apply I = [&](const double2* x, double2* out) {
+        SIE_CUDA_TRY(cudaMemcpyAsync(out, x, sizeof(double2) * nt, cudaMemcpyDeviceToDevice, st));
+        return SIE_OK;
+    };
+    int it = 0;
+    double rr = 0;
+    sie_status s;
+    {
+        Stage s_(c, "constraint_solve");
+        s = fgmres(c, K, nt, S, I, rq, q, op->p.tol_constraint, op->p.constraint_maxit, op->p.constraint_restart, &it,
+                   &rr);
+    }
+    op->stats[4] = std::max(op->stats[4], (double)it);
+    op->stats[5] = std::max(op->stats[5], rr);
+    if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
+    // y = Dg^-1 (v + kappa D^T Lphi q)
+    SIE_CUDA_TRY(cudaMemsetAsync(ph, 0, sizeof(double2) * nt, st));
+    SIE_TRY(spmv(st, (int)nt, a.tri_row_ptr, a.tri_col, a.valLphiNR, q, 1.0, ph));
+    SIE_CUDA_TRY(cudaMemsetAsync(te, 0, sizeof(double2) * ne, st));
+    k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, ph, te);
+    SIE_CUDA_TRY(cudaGetLastError());
+    SIE_TRY(axpby(st, ne, kappa, te, 0.0, te));
+    SIE_TRY(axpby(st, ne, 1.0, v, 1.0, te));
+    k_jacobi<<<nb(ne), 256, 0, st>>>(ne, te, a.dLA, make_double2(1.0, 0.0), y);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+// Exterior AEFIE constraint preconditioner P = [[j k0 Dg, D^T Lphi_NR B], [F D, j k0 I]]
+// applied exactly by block elimination (Schur complement on the currents):
+//   w1 = (j k0)^-1 (Dg - k0^-2 D^T Lphi_NR D)^-1 (v1 - (j k0)^-1 D^T Lphi_NR B v2)
+//   w2 = (v2 - F D w1) / (j k0)
+static sie_status precond_sys(sie_op* op, const double2* x, double2* y)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const DevMesh& M = op->mesh->d;
+    const int64_t ne = M.ne, nt = M.nt;
+    AimOp& X = op->ext;
+    const cplx jk0(0.0, op->k0);
+    double2* v1p = op->pc_e;          // ne
+    double2* sig = op->pc_t;          // nt
+    double2* ph = op->pc_t + nt;      // nt
+    // v1' = v1 - (j k0)^-1 D^T Lphi B v2,  B v2 = -A v2
+    k_sigma<<<nb(nt), 256, 0, st>>>((int)nt, M.area, x + ne, sig);
+    SIE_CUDA_TRY(cudaMemsetAsync(ph, 0, sizeof(double2) * nt, st));
+    SIE_TRY(spmv(st, (int)nt, X.tri_row_ptr, X.tri_col, X.valLphiNR, sig, 1.0, ph));
+    SIE_CUDA_TRY(cudaMemsetAsync(v1p, 0, sizeof(double2) * ne, st));
+    k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, ph, v1p);
+    SIE_CUDA_TRY(cudaGetLastError());
+    SIE_TRY(axpby(st, ne, 1.0, x, -1.0 / jk0, v1p));
+    SIE_TRY(constraint_solve(op, X, 1.0 / (op->k0 * op->k0), op->kcs_out, v1p, y));
+    SIE_TRY(axpby(st, ne, 1.0 / jk0, y, 0.0, y));
+    // w2 = (v2 - F D w1) / (j k0), (F D w1)_t = (D w1)_t / A_t
+    k_D<<<nb(nt), 256, 0, st>>>((int)nt, M, y, ph);
+    SIE_CUDA_TRY(cudaGetLastError());
+    k_jacobi<<<nb(nt), 256, 0, st>>>(nt, ph, nullptr, make_double2(1.0, 0.0), ph);
+    k_fdiv_area<<<nb(nt), 256, 0, st>>>((int)nt, M.area, ph);
+    SIE_CUDA_TRY(cudaGetLastError());
+    SIE_CUDA_TRY(cudaMemcpyAsync(y + ne, x + ne, sizeof(double2) * nt, cudaMemcpyDeviceToDevice, st));
+    SIE_TRY(axpby(st, nt, -1.0 / jk0, ph, 1.0 / jk0, y + ne));
+    return SIE_OK;
+}
+
+sie_status sys_prepare(sie_op* op)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const HostMesh& h = op->mesh->h;
+    // Ix as an edge CSR: (Ix)_mn = I_T f_m . (n x f_n) = c_m c_n A n . ((p_n - c) x (p_m - c))
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(h.ne);
+    for (int64_t t = 0; t < h.nt; t++) {
+        const double* c = &h.cen[3 * t];
+        const double* nr = &h.nrm[3 * t];
+        double p[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int d = 0; d < 3; d++) p[i][d] = h.V[3 * h.T[3 * t + i] + d] - c[d];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double cx = p[j][1] * p[i][2] - p[j][2] * p[i][1];
+                double cy = p[j][2] * p[i][0] - p[j][0] * p[i][2];
+                double cz = p[j][0] * p[i][1] - p[j][1] * p[i][0];
+                double v = h.coef[3 * t + i] * h.coef[3 * t + j] * h.area[t] * (nr[0] * cx + nr[1] * cy + nr[2] * cz);
+                rows[h.tri_edge[3 * t + i]].push_back({h.tri_edge[3 * t + j], v});
+            }
+    }
+    std::vector<int64_t> rp(h.ne + 1, 0);
+    std::vector<int32_t> col;
+    std::vector<double2> val;
+    for (int64_t m = 0; m < h.ne; m++) {
+        auto& r = rows[m];
+        std::sort(r.begin(), r.end(), [](auto& a, auto& b) { return a.first < b.first; });
+        for (size_t k = 0; k < r.size(); k++) {
+            if (!col.empty() && (int64_t)col.size() > rp[m] && col.back() == r[k].first)
+                val.back().x += r[k].second;
+            else {
+                col.push_back(r[k].first);
+                val.push_back(make_double2(r[k].second, 0.0));
+            }
+        }
+        rp[m + 1] = (int64_t)col.size();
+    }
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->ix_row_ptr, sizeof(int64_t) * rp.size(), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->ix_col, sizeof(int32_t) * col.size(), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->ix_val, sizeof(double2) * val.size(), st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(op->ix_row_ptr, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(op->ix_col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(op->ix_val, val.data(), sizeof(double2) * val.size(), cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->elen, sizeof(double) * h.ne, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(op->elen, h.edge_len.data(), sizeof(double) * h.ne, cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->sys_E, sizeof(double2) * h.ne, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->sys_tmp, sizeof(double2) * (h.ne + 2 * h.nt), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->sys_vec, sizeof(double2) * 4 * (h.ne + h.nt), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->cs_e, sizeof(double2) * 2 * h.ne, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->cs_t, sizeof(double2) * 3 * h.nt, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->pc_e, sizeof(double2) * h.ne, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->pc_t, sizeof(double2) * 2 * h.nt, st));
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIE_OK;
+}
+
+void sys_release(sie_op* op)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    op->kin.release(st);
+    op->kout.release(st);
+    op->kcs_in.release(st);
+    op->kcs_out.release(st);
+    for (void* p : {(void*)op->ix_row_ptr, (void*)op->ix_col, (void*)op->ix_val, (void*)op->elen, (void*)op->sys_E,
+                    (void*)op->sys_tmp, (void*)op->sys_vec, (void*)op->cs_e, (void*)op->cs_t, (void*)op->pc_e,
+                    (void*)op->pc_t})
+        if (p) cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);
+}
+
+sie_status sys_matvec(sie_op* op, int which, const double2* x, double2* y)
+{
+    if (which == SIE_OP_SYS) return apply_sys(op, x, y);
+    return apply_Z(op, x, y, nullptr);
+}
+
+sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres)
+{
+    const int64_t n = op->mesh->h.ne + op->mesh->h.nt;
+    Apply A = [&](const double2* u, double2* v) { return apply_sys(op, u, v); };
+    Apply Minv = [&](const double2* u, double2* v) { return precond_sys(op, u, v); };
+    for (int i = 2; i < 6; i++) op->stats[i] = 0;
+    int it = 0;
+    double rr = 0;
+    sie_status s = fgmres(op->mesh->ctx, op->kout, n, A, Minv, b, x, op->p.tol_outer, op->p.maxit, op->p.restart,
+                          &it, &rr);
+    op->stats[0] = it;
+    op->stats[1] = rr;
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    return s;
+}
+
+sie_status sys_rhs(sie_op* op, const double* khat, const double* epol, double2* b)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const DevMesh& M = op->mesh->d;
+    SIE_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(double2) * (M.ne + M.nt), st));
+    k_rhs<<<nb(M.nt), 256, 0, st>>>(M.nt, M, gl_rule(6), op->k0, make_double3(khat[0], khat[1], khat[2]),
+                                    make_double3(epol[0], epol[1], epol[2]), -1.0 / ETA0, b);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, double* rcs)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const DevMesh& M = op->mesh->d;
+    double2* E = op->sys_E;
+    SIE_TRY(apply_Z(op, x, E, nullptr));
+    double *dr = nullptr;
+    double2* dout = nullptr;
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&dr, sizeof(double) * 3 * ndir, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&dout, sizeof(double2) * 6 * ndir, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(dr, rhat, sizeof(double) * 3 * ndir, cudaMemcpyHostToDevice, st));
+    k_far<<<ndir, 256, 0, st>>>(M.nt, M, gl_rule(6), op->k0, dr, x, E, dout);
+    SIE_CUDA_TRY(cudaGetLastError());
+    std::vector<double2> h(6 * ndir);
+    SIE_CUDA_TRY(cudaMemcpyAsync(h.data(), dout, sizeof(double2) * 6 * ndir, cudaMemcpyDeviceToHost, st));
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFreeAsync(dr, st);
+    cudaFreeAsync(dout, st);
+    for (int d = 0; d < ndir; d++) {
+        cplx NH[3], NE[3];
+        for (int k = 0; k < 3; k++) {
+            NH[k] = cplx(h[6 * d + k].x, h[6 * d + k].y);
+            NE[k] = cplx(h[6 * d + 3 + k].x, h[6 * d + 3 + k].y);
+        }
+        double r[3] = {rhat[3 * d], rhat[3 * d + 1], rhat[3 * d + 2]};
+        cplx rn = r[0] * NH[0] + r[1] * NH[1] + r[2] * NH[2];
+        cplx v[3];
+        v[0] = NH[0] - rn * r[0] + (r[1] * NE[2] - r[2] * NE[1]);
+        v[1] = NH[1] - rn * r[1] + (r[2] * NE[0] - r[0] * NE[2]);
+        v[2] = NH[2] - rn * r[2] + (r[0] * NE[1] - r[1] * NE[0]);
+        double s = std::norm(v[0]) + std::norm(v[1]) + std::norm(v[2]);
+        rcs[d] = op->k0 * op->k0 * ETA0 * ETA0 / (4 * M_PI) * s;
+    }
+    return SIE_OK;
+}
+
+}  // namespace sie

@@ -24,10 +24,12 @@ def _icosahedron():
     return v / np.linalg.norm(v, axis=1, keepdims=True), f
 
 
-def icosphere(level, radius=1.0):
+def icosphere(level, radius=1.0, equal_volume=False):
     """Icosahedron refined ``level`` times (each triangle split in 4) and
     projected onto the sphere of the given radius: 20*4**level triangles,
-    30*4**level edges."""
+    30*4**level edges.  equal_volume=True scales the vertices out so that the
+    polyhedron encloses the same volume as the sphere (the flat faces of an
+    inscribed mesh otherwise shrink the scatterer by O(h^2))."""
     v, f = _icosahedron()
     verts = [tuple(x) for x in v]
     for _ in range(level):
@@ -53,6 +55,10 @@ def icosphere(level, radius=1.0):
     n = np.cross(V[f[:, 1]] - V[f[:, 0]], V[f[:, 2]] - V[f[:, 0]])
     flip = np.einsum("ij,ij->i", n, g) < 0
     f[flip] = f[flip][:, [0, 2, 1]]
+    if equal_volume:
+        a, b, c = V[f[:, 0]], V[f[:, 1]], V[f[:, 2]]
+        vol = np.einsum("ij,ij->i", a, np.cross(b, c)).sum() / 6.0
+        V = V * (4.0 / 3.0 * np.pi * radius ** 3 / vol) ** (1.0 / 3.0)
     return V, f.astype(np.int32)
 
 

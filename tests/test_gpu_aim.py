@@ -28,22 +28,6 @@ def k_medium(f, eps_r, sigma, mu_r=1.0):
     return -k if k.imag > 0 else k
 
 
-@pytest.fixture(scope="module")
-def lib():
-    torch = pytest.importorskip("torch")
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    import paper_2003_11679_gb300 as sie
-    from paper_2003_11679_gb300 import build
-    build.build()
-    return sie
-
-
-@pytest.fixture(scope="module")
-def ctx(lib):
-    return lib.Context(0)
-
-
 def _csr_dense(rp, col, val, n):
     A = np.zeros((n, n), complex)
     for r in range(n):
