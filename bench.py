@@ -238,7 +238,15 @@ def run_ours(args):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
-    print(json.dumps(line))
+    print(json.dumps(line, default=_jsonable))
+
+
+def _jsonable(o):
+    if hasattr(o, "item"):
+        return o.item()
+    if hasattr(o, "tolist"):
+        return o.tolist()
+    return str(o)
 
 
 def solve_stats(sie, ctx, args):
@@ -266,7 +274,7 @@ def solve_stats(sie, ctx, args):
     lat = np.array(lat)
     return {"workload": "dielectric-sphere-1920", "tol": 1e-6, "solves": args.solves,
             "solves_per_s": float(len(lat) / lat.sum()), "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "iters": its}
+            "p99_s": float(np.percentile(lat, 99)), "iters": [int(i) for i in its]}
 
 
 def cpu_baseline(wl, args):
@@ -309,7 +317,7 @@ def run_reference(args):
                              "value": cpu["value"]},
             "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}
-    print(json.dumps(line))
+    print(json.dumps(line, default=_jsonable))
 
 
 def main():

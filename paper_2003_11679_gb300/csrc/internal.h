@@ -185,7 +185,7 @@ namespace sie {
 struct KrylovWork {
     int64_t n = 0;
     int m = 0;
-    double2 *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *r = nullptr;
+    double2 *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *r = nullptr, *part = nullptr;
     sie_status alloc(cudaStream_t st, int64_t n_, int m_);
     void release(cudaStream_t st);
 };

@@ -47,29 +47,53 @@ __global__ void k_jacobi(int64_t n, const double2* __restrict__ x, const double2
     y[i] = make_double2((xv.x * q.x + xv.y * q.y) / den, (xv.y * q.x - xv.x * q.y) / den);
 }
 
-// out[j] = sum_k conj(V[j][k]) w[k], one block per basis vector (fixed-order tree)
-__global__ void __launch_bounds__(256) k_dots(int64_t n, const double2* __restrict__ V, int64_t ld,
-                                              const double2* __restrict__ w, double2* __restrict__ out)
+// out[j] = sum_k conj(V[j][k]) w[k] for j < nv: pass 1 writes one partial per
+// (chunk, vector) block, pass 2 sums the partials of each vector in a fixed
+// order (deterministic, and spread over the whole GPU for long vectors)
+constexpr int DOT_CHUNKS = 64;
+__global__ void __launch_bounds__(256) k_dots_part(int64_t n, const double2* __restrict__ V, int64_t ld,
+                                                   const double2* __restrict__ w, double2* __restrict__ part)
 {
-    const double2* v = V + (int64_t)blockIdx.x * ld;
+    const int j = blockIdx.y, c = blockIdx.x;
+    const double2* v = V + (int64_t)j * ld;
+    const int64_t len = (n + DOT_CHUNKS - 1) / DOT_CHUNKS;
+    const int64_t k0 = c * len, k1 = min(n, k0 + len);
     double sr = 0, si = 0;
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         double2 a = v[k], b = w[k];
         sr += a.x * b.x + a.y * b.y;
         si += a.x * b.y - a.y * b.x;
     }
-    __shared__ double rr[256], ri[256];
-    rr[threadIdx.x] = sr;
-    ri[threadIdx.x] = si;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) {
-            rr[threadIdx.x] += rr[threadIdx.x + s];
-            ri[threadIdx.x] += ri[threadIdx.x + s];
-        }
-        __syncthreads();
+    for (int off = 16; off > 0; off >>= 1) {
+        sr += __shfl_down_sync(0xffffffffu, sr, off);
+        si += __shfl_down_sync(0xffffffffu, si, off);
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = make_double2(rr[0], ri[0]);
+    __shared__ double rr[8], ri[8];
+    if ((threadIdx.x & 31) == 0) {
+        rr[threadIdx.x >> 5] = sr;
+        ri[threadIdx.x >> 5] = si;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int i = 0; i < 8; i++) {
+            a += rr[i];
+            b += ri[i];
+        }
+        part[(int64_t)j * DOT_CHUNKS + c] = make_double2(a, b);
+    }
+}
+
+__global__ void k_dots_final(int nv, const double2* __restrict__ part, double2* __restrict__ out)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nv) return;
+    double a = 0, b = 0;
+    for (int c = 0; c < DOT_CHUNKS; c++) {
+        a += part[(int64_t)j * DOT_CHUNKS + c].x;
+        b += part[(int64_t)j * DOT_CHUNKS + c].y;
+    }
+    out[j] = make_double2(a, b);
 }
 
 // w -= sum_j V[j] h[j]   (sgn = -1) or x += sum_j V[j] h[j] (sgn = +1)
@@ -89,6 +113,16 @@ __global__ void k_gemv(int64_t n, int nv, const double2* __restrict__ V, int64_t
 }
 
 static unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// out[0..nv) = V^H w using the partial buffer part (nv * DOT_CHUNKS)
+static sie_status dots(cudaStream_t st, int64_t n, int nv, const double2* V, int64_t ld, const double2* w,
+                       double2* part, double2* out)
+{
+    k_dots_part<<<dim3(DOT_CHUNKS, nv), 256, 0, st>>>(n, V, ld, w, part);
+    k_dots_final<<<(nv + 127) / 128, 128, 0, st>>>(nv, part, out);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
 
 static sie_status axpby(cudaStream_t st, int64_t n, cplx a, const double2* x, cplx b, double2* y)
 {
@@ -111,22 +145,22 @@ sie_status KrylovWork::alloc(cudaStream_t st, int64_t n_, int m_)
     SIE_CUDA_TRY(cudaMallocAsync((void**)&w, sizeof(double2) * n, st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&r, sizeof(double2) * n, st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&h, sizeof(double2) * 2 * (m + 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&part, sizeof(double2) * DOT_CHUNKS * (m + 1), st));
     return SIE_OK;
 }
 
 void KrylovWork::release(cudaStream_t st)
 {
-    for (double2* p : {V, Z, w, h, r})
+    for (double2* p : {V, Z, w, h, r, part})
         if (p) cudaFreeAsync(p, st);
-    V = Z = w = h = r = nullptr;
+    V = Z = w = h = r = part = nullptr;
     n = 0;
     m = 0;
 }
 
-static sie_status dev_norm(cudaStream_t st, int64_t n, const double2* x, double2* tmp, double* out)
+static sie_status dev_norm(cudaStream_t st, int64_t n, const double2* x, double2* part, double2* tmp, double* out)
 {
-    k_dots<<<1, 256, 0, st>>>(n, x, n, x, tmp);
-    SIE_CUDA_TRY(cudaGetLastError());
+    SIE_TRY(dots(st, n, 1, x, n, x, part, tmp));
     double2 v;
     SIE_CUDA_TRY(cudaMemcpyAsync(&v, tmp, sizeof(double2), cudaMemcpyDeviceToHost, st));
     SIE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -144,7 +178,7 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
     SIE_TRY(K.alloc(st, n, restart));
     SIE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
     double bnorm;
-    SIE_TRY(dev_norm(st, n, b, K.h, &bnorm));
+    SIE_TRY(dev_norm(st, n, b, K.part, K.h, &bnorm));
     int it = 0;
     double rel = 1.0;
     if (bnorm == 0.0) {
@@ -168,15 +202,14 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
             SIE_TRY(A(Zj, K.w));
             // CGS2
             for (int pass = 0; pass < 2; pass++) {
-                k_dots<<<j + 1, 256, 0, st>>>(n, K.V, n, K.w, K.h);
-                SIE_CUDA_TRY(cudaGetLastError());
+                SIE_TRY(dots(st, n, j + 1, K.V, n, K.w, K.part, K.h));
                 k_gemv<<<nb(n), 256, 0, st>>>(n, j + 1, K.V, n, K.h, -1.0, K.w);
                 SIE_CUDA_TRY(cudaGetLastError());
                 SIE_CUDA_TRY(cudaMemcpyAsync(pass ? h2.data() : hv.data(), K.h, sizeof(double2) * (j + 1),
                                              cudaMemcpyDeviceToHost, st));
             }
             double hn;
-            SIE_TRY(dev_norm(st, n, K.w, K.h + restart + 1, &hn));  // syncs: hv, h2 valid
+            SIE_TRY(dev_norm(st, n, K.w, K.part, K.h + restart + 1, &hn));  // syncs: hv, h2 valid
             for (int i = 0; i <= j; i++) H[i * restart + j] = hv[i] + h2[i];
             H[(j + 1) * restart + j] = hn;
             if (hn > 0) SIE_TRY(axpby(st, n, cplx(1.0 / hn, 0), K.w, 0.0, K.V + (int64_t)(j + 1) * n));
@@ -226,7 +259,7 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
         SIE_TRY(A(x, K.w));
         SIE_CUDA_TRY(cudaMemcpyAsync(K.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
         SIE_TRY(axpby(st, n, -1.0, K.w, 1.0, K.r));
-        SIE_TRY(dev_norm(st, n, K.r, K.h, &beta));
+        SIE_TRY(dev_norm(st, n, K.r, K.part, K.h, &beta));
         rel = beta / bnorm;
         if (rel < tol) break;
     }
