@@ -152,10 +152,12 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
                         const sie_params* params, sie_op** out);
 sie_status sie_op_destroy(sie_op* op);
 
-/* Replace the solver controls of a built operator: tol_outer, tol_inner,
- * maxit, restart, inner_maxit, tol_constraint, constraint_maxit,
- * constraint_restart are taken from params; grid and quadrature fields are
- * ignored (they are fixed at build time). */
+/* Replace the solver controls of a built operator: precision (grid path of
+ * the system product: SIE_FP64 or SIE_MIXED = complex64 projection, FFT,
+ * spectral multiply and interpolation with FP64 near-region products and
+ * FP64 Krylov), tol_outer, tol_inner, maxit, restart, inner_maxit,
+ * tol_constraint, constraint_maxit, constraint_restart are taken from params;
+ * grid and quadrature fields are ignored (they are fixed at build time). */
 sie_status sie_op_set_solver(sie_op* op, const sie_params* params);
 
 /* Statistics of the last sie_solve on this operator (6 doubles): outer

@@ -105,6 +105,12 @@ __global__ void k_weights(int nt, int Mord, int p, DevMesh M, const int32_t* __r
     o4[3] = w1[2];
 }
 
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
 sie_status aim_weights(sie_op* op)
 {
     cudaStream_t st = op->mesh->ctx->stream;
@@ -120,12 +126,16 @@ sie_status aim_weights(sie_op* op)
     k_weights<<<(nt * S + 127) / 128, 128, 0, st>>>(nt, g.M, p, op->mesh->d, op->base, g.o[0], g.o[1], g.o[2], g.h,
                                                     op->W);
     SIE_CUDA_TRY(cudaGetLastError());
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->W32, sizeof(float) * 4 * (size_t)nt * S, st));
+    k_to_f32<<<(unsigned)((4 * (size_t)nt * S + 255) / 256), 256, 0, st>>>(op->W, op->W32, 4 * (int64_t)nt * S);
+    SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
 }
 
 // ------------------------------------------------------------------ FFT
 // Twiddles exp(-2 pi i k / n), k < n/2, for n = 2^l (l <= 10), concatenated.
 static double2* g_tw[11] = {nullptr};
+static float2* g_tw32[11] = {nullptr};
 static int g_tw_dev[11] = {-1};
 
 static sie_status twiddles(int logn, cudaStream_t st, double2** out)
@@ -145,9 +155,23 @@ static sie_status twiddles(int logn, cudaStream_t st, double2** out)
     double2* d = nullptr;
     SIE_CUDA_TRY(cudaMalloc((void**)&d, sizeof(double2) * h.size()));
     SIE_CUDA_TRY(cudaMemcpy(d, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice));
+    std::vector<float2> hf(h.size());
+    for (size_t k = 0; k < h.size(); k++) hf[k] = make_float2((float)h[k].x, (float)h[k].y);
+    float2* f = nullptr;
+    SIE_CUDA_TRY(cudaMalloc((void**)&f, sizeof(float2) * hf.size()));
+    SIE_CUDA_TRY(cudaMemcpy(f, hf.data(), sizeof(float2) * hf.size(), cudaMemcpyHostToDevice));
     g_tw[logn] = d;
+    g_tw32[logn] = f;
     g_tw_dev[logn] = dev;
     *out = d;
+    return SIE_OK;
+}
+
+static sie_status twiddles(int logn, cudaStream_t st, float2** out)
+{
+    double2* d = nullptr;
+    SIE_TRY(twiddles(logn, st, &d));
+    *out = g_tw32[logn];
     return SIE_OK;
 }
 
@@ -162,13 +186,22 @@ struct PassGeom {
 
 // One CTA transforms PB pencils of length n = 2^LOGN held in shared memory.
 // Load at bit-reversed positions, log2(n) radix-2 DIT stages, store.
-template <int LOGN, int PB>
-__global__ void __launch_bounds__(256) k_fft_pass(const double2* in, double2* out,  // may alias (in place)
-                                                  const double2* __restrict__ tw, int inv, PassGeom G)
+template <class C>
+__device__ __forceinline__ C cmake(double a, double b);
+template <>
+__device__ __forceinline__ double2 cmake<double2>(double a, double b) { return make_double2(a, b); }
+template <>
+__device__ __forceinline__ float2 cmake<float2>(double a, double b) { return make_float2((float)a, (float)b); }
+
+// C = double2 (FP64 path) or float2 (complex64 grid path)
+template <int LOGN, int PB, class C>
+__global__ void __launch_bounds__(256) k_fft_pass(const C* in, C* out,  // may alias (in place)
+                                                  const C* __restrict__ tw, int inv, PassGeom G)
 {
     constexpr int n = 1 << LOGN;
     constexpr int pitch = n + 1;
-    extern __shared__ double2 sm[];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
     const int64_t p0 = (int64_t)blockIdx.x * PB;
     // load (zero padded)
     for (int idx = threadIdx.x; idx < PB * n; idx += blockDim.x) {
@@ -181,7 +214,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(const double2* in, double2* ou
             j = idx / PB;
         }
         int64_t p = p0 + pl;
-        double2 v = make_double2(0.0, 0.0);
+        C v = cmake<C>(0.0, 0.0);
         if (p < G.npencil && j < G.n_in) {
             int64_t b = (p % G.L) * G.slo_in + (p / G.L) * G.shi_in;
             v = in[b + (int64_t)j * G.st_in];
@@ -196,12 +229,19 @@ __global__ void __launch_bounds__(256) k_fft_pass(const double2* in, double2* ou
             int pl = bfly / (n / 2), bb = bfly % (n / 2);
             int grp = bb >> (s - 1), pos = bb & (half - 1);
             int i0 = grp * 2 * half + pos, i1 = i0 + half;
-            double2 w = tw[pos << (LOGN - s)];
+            C w = tw[pos << (LOGN - s)];
             if (inv) w.y = -w.y;
-            double2 u = sm[pl * pitch + i0], v = sm[pl * pitch + i1];
-            double2 vw = make_double2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
-            sm[pl * pitch + i0] = make_double2(u.x + vw.x, u.y + vw.y);
-            sm[pl * pitch + i1] = make_double2(u.x - vw.x, u.y - vw.y);
+            C u = sm[pl * pitch + i0], v = sm[pl * pitch + i1];
+            C vw;
+            vw.x = v.x * w.x - v.y * w.y;
+            vw.y = v.x * w.y + v.y * w.x;
+            C a0, a1;
+            a0.x = u.x + vw.x;
+            a0.y = u.y + vw.y;
+            a1.x = u.x - vw.x;
+            a1.y = u.y - vw.y;
+            sm[pl * pitch + i0] = a0;
+            sm[pl * pitch + i1] = a1;
         }
         __syncthreads();
     }
@@ -222,26 +262,27 @@ __global__ void __launch_bounds__(256) k_fft_pass(const double2* in, double2* ou
     }
 }
 
-template <int LOGN>
-static sie_status launch_pass_n(cudaStream_t st, const double2* in, double2* out, int inv, const PassGeom& G)
+template <int LOGN, class C>
+static sie_status launch_pass_n(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G)
 {
     constexpr int n = 1 << LOGN;
     constexpr int PB = (n >= 512) ? 8 : 16;
-    double2* tw = nullptr;
+    C* tw = nullptr;
     SIE_TRY(twiddles(LOGN, st, &tw));
-    size_t smem = sizeof(double2) * PB * (n + 1);
+    size_t smem = sizeof(C) * PB * (n + 1);
     static bool attr = false;
     if (!attr) {
-        SIE_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<LOGN, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SIE_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<LOGN, PB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
     unsigned blocks = (unsigned)((G.npencil + PB - 1) / PB);
-    k_fft_pass<LOGN, PB><<<blocks, 256, smem, st>>>(in, out, tw, inv, G);
+    k_fft_pass<LOGN, PB, C><<<blocks, 256, smem, st>>>(in, out, tw, inv, G);
     SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
 }
 
-static sie_status launch_pass(cudaStream_t st, int n, const double2* in, double2* out, int inv, const PassGeom& G)
+template <class C>
+static sie_status launch_pass(cudaStream_t st, int n, const C* in, C* out, int inv, const PassGeom& G)
 {
     switch (n) {
         case 16: return launch_pass_n<4>(st, in, out, inv, G);
@@ -260,7 +301,8 @@ static sie_status launch_pass(cudaStream_t st, int n, const double2* in, double2
 // full n grid already in buf) into the full spectrum in buf.
 // dir = +1: inverse of the spectrum in buf; prune = 1 writes only the physical
 // N box into the compact array `src` (used as output), prune = 0 keeps n^3 in buf.
-sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune, sie_ctx* pc)
+template <class C>
+static sie_status fft3d_t(cudaStream_t st, C* buf, const C* src, const GridDesc& g, int dir, int prune, sie_ctx* pc)
 {
     const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int64_t Nx = prune ? g.N[0] : nx, Ny = prune ? g.N[1] : ny, Nz = prune ? g.N[2] : nz;
@@ -295,7 +337,7 @@ sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDe
             Stage s_(pc, "fft_inv_y");
             SIE_TRY(launch_pass(st, (int)ny, buf, buf, 1, Y));
         }
-        double2* dst = prune ? const_cast<double2*>(src) : buf;
+        C* dst = prune ? const_cast<C*>(src) : buf;
         PassGeom X{(int)nx, (int)Nx, Ny * Nz, (int)Ny, nx, pyz, 1, prune ? Nx : nx, prune ? Nx * Ny : pyz, 1, 1};
         {
             Stage s_(pc, "fft_inv_x");
@@ -303,6 +345,16 @@ sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDe
         }
     }
     return SIE_OK;
+}
+
+sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune, sie_ctx* pc)
+{
+    return fft3d_t(st, buf, src, g, dir, prune, pc);
+}
+
+sie_status fft3d(cudaStream_t st, float2* buf, const float2* src, const GridDesc& g, int dir, int prune, sie_ctx* pc)
+{
+    return fft3d_t(st, buf, src, g, dir, prune, pc);
 }
 
 // ------------------------------------------------------------------ kernel spectra
@@ -365,7 +417,10 @@ sie_status aim_spectra(sie_op* op, AimOp& a)
     SIE_CUDA_TRY(cudaMallocAsync((void**)&a.spec, sizeof(double2) * 4 * nn, st));
     k_sample<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(g, a.kr, a.ki, a.spec, nn);
     SIE_CUDA_TRY(cudaGetLastError());
-    for (int c = 0; c < 4; c++) SIE_TRY(fft3d(st, a.spec + c * nn, nullptr, g, -1, 0, nullptr));
+    for (int c = 0; c < 4; c++) SIE_TRY(fft3d(st, a.spec + c * nn, (const double2*)nullptr, g, -1, 0, nullptr));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&a.spec32, sizeof(float2) * 4 * nn, st));
+    k_to_c64<<<(unsigned)((4 * nn + 255) / 256), 256, 0, st>>>(a.spec, a.spec32, 4 * nn);
+    SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
 }
 
@@ -610,7 +665,7 @@ sie_status sie_op_destroy(sie_op* op)
     sys_release(op);
     free_aim(op->ext);
     free_aim(op->inn);
-    void* ptrs[] = {op->base, op->W, op->ws.bufs, op->ws.src, op->xtmp};
+    void* ptrs[] = {op->base, op->W, op->W32, op->ws.bufs, op->ws.src, op->xtmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete op;

@@ -566,6 +566,7 @@ sie_status sie_op_set_solver(sie_op* op, const sie_params* p)
     op->p.tol_constraint = p->tol_constraint;
     op->p.constraint_maxit = p->constraint_maxit;
     op->p.constraint_restart = p->constraint_restart;
+    if (p->precision == SIE_FP64 || p->precision == SIE_MIXED) op->p.precision = p->precision;
     return SIE_OK;
 }
 

@@ -199,6 +199,7 @@ struct sie_op {
     sie::AimOp ext, inn;
     int32_t* base = nullptr;        // stencil base (nt*3), shared by ext and inner grids
     double* W = nullptr;            // weights nt * S * 4
+    float* W32 = nullptr;           // complex64 grid path copy of W
     sie::Workspace ws;
     double2* xtmp = nullptr;        // scratch vectors (ne * 4)
     double build_ms[4] = {0, 0, 0, 0};  // weights+spectra, exterior near, interior near, host lists
@@ -232,5 +233,7 @@ sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, doubl
 sie_status sys_rhs(sie_op* op, const double* khat, const double* epol, double2* b);
 sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, double* rcs);
 sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune,
+                 sie_ctx* prof_ctx);
+sie_status fft3d(cudaStream_t st, float2* buf, const float2* src, const GridDesc& g, int dir, int prune,
                  sie_ctx* prof_ctx);
 }  // namespace sie

@@ -309,6 +309,122 @@ __global__ void k_project_sys(int nt, int S, int Mord, DevMesh M, const int32_t*
     atomicAdd(&d->y, -r.y * w[0]);
 }
 
+// complex64 grid path (SIE_MIXED): same projection in FP32 with FP32 atomics
+__global__ void k_project_sys32(int nt, int S, int Mord, DevMesh M, const int32_t* __restrict__ base,
+                                const float* __restrict__ W, const double2* __restrict__ H,
+                                const double2* __restrict__ E, const double2* __restrict__ rho, GridDesc g,
+                                float2* __restrict__ src, int64_t Ng)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nt * S) return;
+    int t = idx / S, u = idx % S;
+    const int Mp = Mord + 1;
+    int nx = base[3 * t] + u % Mp, ny = base[3 * t + 1] + (u / Mp) % Mp, nz = base[3 * t + 2] + u / (Mp * Mp);
+    int64_t node = ((int64_t)nz * g.N[1] + ny) * g.N[0] + nx;
+    const float4 w = *reinterpret_cast<const float4*>(W + (size_t)idx * 4);
+    const float ww[4] = {w.x, w.y, w.z, w.w};
+    for (int f = 0; f < 2; f++) {
+        const double2* x = f ? E : H;
+        float alr = 0, ali = 0, ber[3] = {0, 0, 0}, bei[3] = {0, 0, 0};
+        for (int i = 0; i < 3; i++) {
+            double2 xv = x[M.tri_edge[3 * t + i]];
+            float c = (float)M.coef[3 * t + i];
+            float xr = (float)xv.x, xi = (float)xv.y;
+            alr += c * xr;
+            ali += c * xi;
+            for (int a = 0; a < 3; a++) {
+                float qq = c * (float)M.q[9 * t + 3 * i + a];
+                ber[a] += qq * xr;
+                bei[a] += qq * xi;
+            }
+        }
+        for (int a = 0; a < 3; a++) {
+            float2* d = src + (3 * f + a) * Ng + node;
+            atomicAdd(&d->x, alr * ww[1 + a] + ber[a] * ww[0]);
+            atomicAdd(&d->y, ali * ww[1 + a] + bei[a] * ww[0]);
+        }
+    }
+    double2 r = rho[t];
+    float2* d = src + 6 * Ng + node;
+    atomicAdd(&d->x, -(float)r.x * ww[0]);
+    atomicAdd(&d->y, -(float)r.y * ww[0]);
+}
+
+__global__ void k_specmul_sys32(const float2* __restrict__ spec, float2* __restrict__ buf, int64_t nn, float k0)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    auto mul = [](float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
+    float2 G = spec[i], gx = spec[nn + i], gy = spec[2 * nn + i], gz = spec[3 * nn + i];
+    float2 jG = make_float2(-k0 * G.y, k0 * G.x);
+    float2 mx = buf[3 * nn + i], my = buf[4 * nn + i], mz = buf[5 * nn + i];
+    float2 cx = mul(gy, mz), cy = mul(gz, mx), cz = mul(gx, my);
+    float2 dx = mul(gz, my), dy = mul(gx, mz), dz = mul(gy, mx);
+    float2 a0 = mul(jG, buf[i]), a1 = mul(jG, buf[nn + i]), a2 = mul(jG, buf[2 * nn + i]);
+    buf[i] = make_float2(a0.x - (cx.x - dx.x), a0.y - (cx.y - dx.y));
+    buf[nn + i] = make_float2(a1.x - (cy.x - dy.x), a1.y - (cy.y - dy.y));
+    buf[2 * nn + i] = make_float2(a2.x - (cz.x - dz.x), a2.y - (cz.y - dz.y));
+    buf[3 * nn + i] = mul(G, buf[6 * nn + i]);
+}
+
+// W = P^T on the complex64 grids: FP32 gathers and sums, FP64 edge coefficients
+__global__ void k_interp32(int nt, int S, int Mord, DevMesh M, const int32_t* __restrict__ base,
+                           const float* __restrict__ W, const float2* __restrict__ out, GridDesc g, int64_t Ng,
+                           double2* __restrict__ y)
+{
+    int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x & 31;
+    if (t >= nt) return;
+    const int Mp = Mord + 1;
+    float s1r = 0, s1i = 0, t0r[3] = {0, 0, 0}, t0i[3] = {0, 0, 0}, p0r = 0, p0i = 0;
+    for (int u = lane; u < S; u += 32) {
+        int nx = base[3 * t] + u % Mp, ny = base[3 * t + 1] + (u / Mp) % Mp, nz = base[3 * t + 2] + u / (Mp * Mp);
+        int64_t node = ((int64_t)nz * g.N[1] + ny) * g.N[0] + nx;
+        const float4 w = *reinterpret_cast<const float4*>(W + ((size_t)t * S + u) * 4);
+        const float w1[3] = {w.y, w.z, w.w};
+        for (int a = 0; a < 3; a++) {
+            float2 A = out[a * Ng + node];
+            s1r += w1[a] * A.x;
+            s1i += w1[a] * A.y;
+            t0r[a] += w.x * A.x;
+            t0i[a] += w.x * A.y;
+        }
+        float2 P = out[3 * Ng + node];
+        p0r += w.x * P.x;
+        p0i += w.x * P.y;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        s1r += __shfl_down_sync(0xffffffffu, s1r, off);
+        s1i += __shfl_down_sync(0xffffffffu, s1i, off);
+        p0r += __shfl_down_sync(0xffffffffu, p0r, off);
+        p0i += __shfl_down_sync(0xffffffffu, p0i, off);
+        for (int a = 0; a < 3; a++) {
+            t0r[a] += __shfl_down_sync(0xffffffffu, t0r[a], off);
+            t0i[a] += __shfl_down_sync(0xffffffffu, t0i[a], off);
+        }
+    }
+    if (lane < 3) {
+        int i = lane;
+        double S1r = __shfl_sync(0x7u, s1r, 0), S1i = __shfl_sync(0x7u, s1i, 0);
+        double P0r = __shfl_sync(0x7u, p0r, 0), P0i = __shfl_sync(0x7u, p0i, 0);
+        double T0r[3], T0i[3];
+        for (int a = 0; a < 3; a++) {
+            T0r[a] = __shfl_sync(0x7u, t0r[a], 0);
+            T0i[a] = __shfl_sync(0x7u, t0i[a], 0);
+        }
+        double vr = S1r + 2.0 * P0r, vi = S1i + 2.0 * P0i;
+        for (int a = 0; a < 3; a++) {
+            double qq = M.q[9 * t + 3 * i + a];
+            vr += qq * T0r[a];
+            vi += qq * T0i[a];
+        }
+        double c = M.coef[3 * t + i];
+        double2* d = y + M.tri_edge[3 * t + i];
+        atomicAdd(&d->x, c * vr);
+        atomicAdd(&d->y, c * vi);
+    }
+}
+
 // A_a = j k0 G J_a - (Ggrad x M)_a into grids 0..2, Phi = G rho into grid 3
 __global__ void k_specmul_sys(const double2* __restrict__ spec, double2* __restrict__ buf, int64_t nn, double k0)
 {
@@ -585,26 +701,50 @@ static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
     int S = (g.M + 1) * (g.M + 1) * (g.M + 1);
     int64_t Ng = (int64_t)g.N[0] * g.N[1] * g.N[2];
     int64_t nn = (int64_t)g.n[0] * g.n[1] * g.n[2];
-    double2* src = op->ws.src;
-    double2* buf = op->ws.bufs;
-    {
-        Stage s_(c, "project_sys");
-        SIE_CUDA_TRY(cudaMemsetAsync(src, 0, sizeof(double2) * 7 * Ng, st));
-        k_project_sys<<<(unsigned)((M.nt * S + 255) / 256), 256, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, H, E, rho,
-                                                                           g, src, Ng);
-        SIE_CUDA_TRY(cudaGetLastError());
-    }
-    for (int k = 0; k < 7; k++) SIE_TRY(fft3d(st, buf + k * nn, src + k * Ng, g, -1, 1, c));
-    {
-        Stage s_(c, "specmul_sys");
-        k_specmul_sys<<<nb(nn), 256, 0, st>>>(X.spec, buf, nn, op->k0);
-        SIE_CUDA_TRY(cudaGetLastError());
-    }
-    for (int k = 0; k < 4; k++) SIE_TRY(fft3d(st, buf + k * nn, src + k * Ng, g, +1, 1, c));
     SIE_CUDA_TRY(cudaMemsetAsync(y1, 0, sizeof(double2) * ne, st));
-    {
-        Stage s_(c, "interp");
-        SIE_TRY(aim_interp(op, src, 1, make_double2(1.0, 0.0), y1));
+    if (op->p.precision == SIE_MIXED) {
+        float2* src = reinterpret_cast<float2*>(op->ws.src);
+        float2* buf = reinterpret_cast<float2*>(op->ws.bufs);
+        {
+            Stage s_(c, "project_sys32");
+            SIE_CUDA_TRY(cudaMemsetAsync(src, 0, sizeof(float2) * 7 * Ng, st));
+            k_project_sys32<<<(unsigned)((M.nt * S + 255) / 256), 256, 0, st>>>(M.nt, S, g.M, M, op->base, op->W32, H,
+                                                                                 E, rho, g, src, Ng);
+            SIE_CUDA_TRY(cudaGetLastError());
+        }
+        for (int k = 0; k < 7; k++) SIE_TRY(fft3d(st, buf + k * nn, src + k * Ng, g, -1, 1, c));
+        {
+            Stage s_(c, "specmul_sys32");
+            k_specmul_sys32<<<nb(nn), 256, 0, st>>>(X.spec32, buf, nn, (float)op->k0);
+            SIE_CUDA_TRY(cudaGetLastError());
+        }
+        for (int k = 0; k < 4; k++) SIE_TRY(fft3d(st, buf + k * nn, src + k * Ng, g, +1, 1, c));
+        {
+            Stage s_(c, "interp32");
+            k_interp32<<<(M.nt + 3) / 4, 128, 0, st>>>(M.nt, S, g.M, M, op->base, op->W32, src, g, Ng, y1);
+            SIE_CUDA_TRY(cudaGetLastError());
+        }
+    } else {
+        double2* src = op->ws.src;
+        double2* buf = op->ws.bufs;
+        {
+            Stage s_(c, "project_sys");
+            SIE_CUDA_TRY(cudaMemsetAsync(src, 0, sizeof(double2) * 7 * Ng, st));
+            k_project_sys<<<(unsigned)((M.nt * S + 255) / 256), 256, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, H, E,
+                                                                               rho, g, src, Ng);
+            SIE_CUDA_TRY(cudaGetLastError());
+        }
+        for (int k = 0; k < 7; k++) SIE_TRY(fft3d(st, buf + k * nn, src + k * Ng, g, -1, 1, c));
+        {
+            Stage s_(c, "specmul_sys");
+            k_specmul_sys<<<nb(nn), 256, 0, st>>>(X.spec, buf, nn, op->k0);
+            SIE_CUDA_TRY(cudaGetLastError());
+        }
+        for (int k = 0; k < 4; k++) SIE_TRY(fft3d(st, buf + k * nn, src + k * Ng, g, +1, 1, c));
+        {
+            Stage s_(c, "interp");
+            SIE_TRY(aim_interp(op, src, 1, make_double2(1.0, 0.0), y1));
+        }
     }
     {
         Stage s_(c, "spmv_sys");

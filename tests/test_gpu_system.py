@@ -100,3 +100,36 @@ def test_solve_rcs_matches_mie(lib, case, request):
     ref = mie.bistatic_rcs(th, 0.0, c.radius, c.f, c.eps_r, c.sigma)
     print(case, "iters", it[0], "relres", rr[0], "rcs/mie-1", rcs / ref - 1)
     assert np.abs(rcs / ref - 1).max() < 0.01
+
+
+@pytest.mark.parametrize("case", ["diel", "lossy"])
+def test_mixed_precision_system_product(lib, case, request):
+    """Complex64 grid path (SIE_MIXED): the system product stays within 1e-5 of
+    the FP64 product (FP32 rounding of the grid part only; near-region
+    products and all vectors stay FP64)."""
+    c = request.getfixturevalue(case)
+    x = np.concatenate([cn_vector(c.ne, 81), cn_vector(c.nt, 82)])
+    y64 = c.op.matvec(lib.SIE_OP_SYS, x)
+    c.op.set_solver(precision=lib.SIE_MIXED)
+    try:
+        y32 = c.op.matvec(lib.SIE_OP_SYS, x)
+    finally:
+        c.op.set_solver(precision=lib.SIE_FP64)
+    err = np.linalg.norm(y32 - y64) / np.linalg.norm(y64)
+    print(case, "mixed vs fp64", err)
+    assert err <= 1e-5
+
+
+def test_mixed_precision_solve_rcs(lib, diel):
+    c = diel
+    c.op.set_solver(precision=lib.SIE_MIXED)
+    try:
+        b = c.op.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
+        x, it, rr = c.op.solve(b)
+        th = np.linspace(0.3, np.pi, 9)
+        dirs = np.stack([np.sin(th), 0 * th, -np.cos(th)], 1)
+        rcs = c.op.rcs(x, dirs)
+    finally:
+        c.op.set_solver(precision=lib.SIE_FP64)
+    ref = mie.bistatic_rcs(th, 0.0, c.radius, c.f, c.eps_r, c.sigma)
+    assert np.abs(rcs / ref - 1).max() < 0.01
