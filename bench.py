@@ -191,7 +191,6 @@ def run_ours(args):
         # complex64 grid path (SIE_MIXED) on the same workload
         op.set_solver(precision=sie.SIE_MIXED)
         y64 = y.clone()
-        op.matvec(sie.SIE_OP_SYS, x, y64)  # FP64 reference product of this x
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
@@ -212,7 +211,8 @@ def run_ours(args):
         op.matvec(sie.SIE_OP_SYS, x, y)
         op.set_solver(precision=sie.SIE_FP64)
         torch.cuda.synchronize()
-        mixed_err = float((y - y64).abs().norm() / y64.abs().norm())
+        # current rows (the grid product lives there; the charge rows are exact in both)
+        mixed_err = float((y[:ne] - y64[:ne]).abs().norm() / y64[:ne].abs().norm())
     solves = solve_stats(sie, ctx, args) if not args.no_solve else None
     if world > 1:
         t = torch.tensor([ms, e2e_s], device=f"cuda:{local}", dtype=torch.float64)
