@@ -186,6 +186,10 @@ struct KrylovWork {
     int64_t n = 0;
     int m = 0;
     double2 *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *r = nullptr, *part = nullptr;
+    double2* Hd = nullptr;          // Hessenberg, rotations, g, y (device)
+    double* sc = nullptr;           // |b|, beta, per-iteration relative residuals (device)
+    double* resid_h = nullptr;      // pinned copies of the residuals
+    std::vector<cudaEvent_t> ev;    // one per iteration: residual copy done
     sie_status alloc(cudaStream_t st, int64_t n_, int m_);
     void release(cudaStream_t st);
 };

@@ -144,41 +144,158 @@ sie_status KrylovWork::alloc(cudaStream_t st, int64_t n_, int m_)
     SIE_CUDA_TRY(cudaMallocAsync((void**)&Z, sizeof(double2) * m * n, st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&w, sizeof(double2) * n, st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&r, sizeof(double2) * n, st));
-    SIE_CUDA_TRY(cudaMallocAsync((void**)&h, sizeof(double2) * 2 * (m + 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&h, sizeof(double2) * 4 * (m + 2), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&part, sizeof(double2) * DOT_CHUNKS * (m + 1), st));
+    // Hessenberg (m+1) x m, rotations cs, sn, rhs g, solution y
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&Hd, sizeof(double2) * ((m + 1) * m + 2 * m + 2 * (m + 1)), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&sc, sizeof(double) * (8 + m + 1), st));
+    SIE_CUDA_TRY(cudaMallocHost((void**)&resid_h, sizeof(double) * (m + 1)));
+    ev.resize(m + 1);
+    for (auto& e : ev) SIE_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return SIE_OK;
 }
 
 void KrylovWork::release(cudaStream_t st)
 {
-    for (double2* p : {V, Z, w, h, r, part})
+    for (double2* p : {V, Z, w, h, r, part, Hd})
         if (p) cudaFreeAsync(p, st);
-    V = Z = w = h = r = part = nullptr;
+    if (sc) cudaFreeAsync(sc, st);
+    if (resid_h) {
+        cudaStreamSynchronize(st);
+        cudaFreeHost(resid_h);
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    ev.clear();
+    V = Z = w = h = r = part = Hd = nullptr;
+    sc = nullptr;
+    resid_h = nullptr;
     n = 0;
     m = 0;
 }
 
-static sie_status dev_norm(cudaStream_t st, int64_t n, const double2* x, double2* part, double2* tmp, double* out)
+// ------------------------------------------------------------------ device-side GMRES pieces
+__device__ __forceinline__ double2 cm(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cj(double2 a) { return make_double2(a.x, -a.y); }
+
+// sc layout: [0] |b|, [1] beta of the current cycle, [3 + j] relative residual after iteration j
+// V0 = r / |r|; g = (|r|, 0, ...), dot2 = r^H r
+__global__ void k_gm_start(int64_t n, const double2* __restrict__ r, const double2* __restrict__ dot2,
+                           double2* __restrict__ V0, double2* __restrict__ g, int m, double* __restrict__ sc,
+                           int set_bnorm)
 {
-    SIE_TRY(dots(st, n, 1, x, n, x, part, tmp));
-    double2 v;
-    SIE_CUDA_TRY(cudaMemcpyAsync(&v, tmp, sizeof(double2), cudaMemcpyDeviceToHost, st));
-    SIE_CUDA_TRY(cudaStreamSynchronize(st));
-    *out = std::sqrt(std::max(v.x, 0.0));
-    return SIE_OK;
+    double beta = sqrt(fmax(dot2[0].x, 0.0));
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        double s = beta > 0 ? 1.0 / beta : 0.0;
+        V0[i] = make_double2(r[i].x * s, r[i].y * s);
+    }
+    if (i == 0) {
+        for (int k = 0; k <= m; k++) g[k] = make_double2(0, 0);
+        g[0] = make_double2(beta, 0);
+        if (set_bnorm) sc[0] = beta;
+        sc[1] = beta;
+    }
+}
+
+// column j of H from the two Gram-Schmidt passes; V_{j+1} = w / |w|
+__global__ void k_gm_next(int64_t n, int j, int m, const double2* __restrict__ h1, const double2* __restrict__ h2,
+                          const double2* __restrict__ wdot, const double2* __restrict__ w, double2* __restrict__ Vn,
+                          double2* __restrict__ H)
+{
+    double hn = sqrt(fmax(wdot[0].x, 0.0));
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        double s = hn > 0 ? 1.0 / hn : 0.0;
+        Vn[i] = make_double2(w[i].x * s, w[i].y * s);
+    }
+    if (i <= j) H[i * m + j] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+    if (i == 0) H[(j + 1) * m + j] = make_double2(hn, 0);
+}
+
+// apply the previous rotations to column j, form rotation j (c real), update
+// g; relative residual |g[j+1]| / |b| to sc[3 + j]
+__global__ void k_gm_givens(int j, int m, double2* __restrict__ H, double2* __restrict__ cs, double2* __restrict__ sn,
+                            double2* __restrict__ g, double* __restrict__ sc)
+{
+    for (int i = 0; i < j; i++) {
+        double2 a = H[i * m + j], b = H[(i + 1) * m + j];
+        double2 sb = cm(sn[i], b), ta = cm(cj(sn[i]), a);
+        H[i * m + j] = make_double2(cs[i].x * a.x + sb.x, cs[i].x * a.y + sb.y);
+        H[(i + 1) * m + j] = make_double2(cs[i].x * b.x - ta.x, cs[i].x * b.y - ta.y);
+    }
+    double2 a = H[j * m + j], b = H[(j + 1) * m + j];
+    double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+    double den = hypot(aa, bb);
+    double2 c, s;
+    if (aa == 0.0) {
+        c = make_double2(0, 0);
+        s = make_double2(1, 0);
+    } else {
+        c = make_double2(aa / den, 0);
+        s = cm(make_double2(a.x / aa, a.y / aa), cj(b));
+        s.x /= den;
+        s.y /= den;
+    }
+    cs[j] = c;
+    sn[j] = s;
+    double2 sb = cm(s, b);
+    H[j * m + j] = make_double2(c.x * a.x + sb.x, c.x * a.y + sb.y);
+    H[(j + 1) * m + j] = make_double2(0, 0);
+    double2 gj = g[j];
+    double2 t = cm(cj(s), gj);
+    g[j] = make_double2(c.x * gj.x, c.x * gj.y);
+    g[j + 1] = make_double2(-t.x, -t.y);
+    sc[3 + j] = (sc[0] > 0) ? hypot(g[j + 1].x, g[j + 1].y) / sc[0] : 0.0;
+}
+
+// y = R^-1 g (upper triangular, size jend + 1)
+__global__ void k_gm_backsub(int jend, int m, const double2* __restrict__ H, const double2* __restrict__ g,
+                             double2* __restrict__ y)
+{
+    for (int i = jend; i >= 0; i--) {
+        double2 s = g[i];
+        for (int k = i + 1; k <= jend; k++) {
+            double2 t = cm(H[i * m + k], y[k]);
+            s.x -= t.x;
+            s.y -= t.y;
+        }
+        double2 d = H[i * m + i];
+        double den = d.x * d.x + d.y * d.y;
+        y[i] = den > 0 ? make_double2((s.x * d.x + s.y * d.y) / den, (s.y * d.x - s.x * d.y) / den)
+                       : make_double2(0, 0);
+    }
 }
 
 // Right-preconditioned restarted flexible GMRES, zero initial guess; the
 // monitored residual is the true residual of A x = b.  Arnoldi in FP64 with
-// classical Gram-Schmidt applied twice.
+// classical Gram-Schmidt applied twice.  Everything stays on the device: the
+// Hessenberg column, the Givens rotations and the back substitution are tiny
+// kernels; the host reads each iteration's residual LAG iterations later
+// (event on a pinned copy), so the GPU does not wait on host round trips.
+// Up to LAG extra iterations may run after convergence (they only lower the
+// residual).
 static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, const Apply& Minv, const double2* b,
                          double2* x, double tol, int maxit, int restart, int* iters_out, double* relres_out)
 {
     cudaStream_t st = c->stream;
     SIE_TRY(K.alloc(st, n, restart));
+    const int m = restart;
+    double2* H = K.Hd;
+    double2* cs = K.Hd + (m + 1) * m;
+    double2* sn = cs + m;
+    double2* g = sn + m;
+    double2* y = g + (m + 1);
+    double2* h1 = K.h;
+    double2* h2 = K.h + (m + 2);
+    double2* wd = K.h + 2 * (m + 2);
     SIE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
-    double bnorm;
-    SIE_TRY(dev_norm(st, n, b, K.part, K.h, &bnorm));
+    SIE_CUDA_TRY(cudaMemcpyAsync(K.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+    SIE_TRY(dots(st, n, 1, K.r, n, K.r, K.part, wd));
+    k_gm_start<<<nb(n), 256, 0, st>>>(n, K.r, wd, K.V, g, m, K.sc, 1);
+    SIE_CUDA_TRY(cudaGetLastError());
+    SIE_CUDA_TRY(cudaMemcpyAsync(K.resid_h, K.sc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    const double bnorm = K.resid_h[0];
     int it = 0;
     double rel = 1.0;
     if (bnorm == 0.0) {
@@ -186,81 +303,54 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
         if (relres_out) *relres_out = 0.0;
         return SIE_OK;
     }
-    SIE_CUDA_TRY(cudaMemcpyAsync(K.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
-    double beta = bnorm;
-    std::vector<cplx> H((restart + 1) * restart), g(restart + 1), cs(restart), sn(restart), hv(restart + 1),
-        h2(restart + 1);
+    const int LAG = 2;
     while (true) {
-        SIE_TRY(axpby(st, n, cplx(1.0 / beta, 0), K.r, 0.0, K.V));
-        std::fill(g.begin(), g.end(), cplx(0));
-        g[0] = beta;
-        int j = 0, jend = -1;
-        for (; j < restart; j++) {
+        int j = 0;
+        bool conv = false;
+        for (; j < m && it < maxit; j++) {
             double2* Vj = K.V + (int64_t)j * n;
             double2* Zj = K.Z + (int64_t)j * n;
             SIE_TRY(Minv(Vj, Zj));
             SIE_TRY(A(Zj, K.w));
-            // CGS2
-            for (int pass = 0; pass < 2; pass++) {
-                SIE_TRY(dots(st, n, j + 1, K.V, n, K.w, K.part, K.h));
-                k_gemv<<<nb(n), 256, 0, st>>>(n, j + 1, K.V, n, K.h, -1.0, K.w);
-                SIE_CUDA_TRY(cudaGetLastError());
-                SIE_CUDA_TRY(cudaMemcpyAsync(pass ? h2.data() : hv.data(), K.h, sizeof(double2) * (j + 1),
-                                             cudaMemcpyDeviceToHost, st));
-            }
-            double hn;
-            SIE_TRY(dev_norm(st, n, K.w, K.part, K.h + restart + 1, &hn));  // syncs: hv, h2 valid
-            for (int i = 0; i <= j; i++) H[i * restart + j] = hv[i] + h2[i];
-            H[(j + 1) * restart + j] = hn;
-            if (hn > 0) SIE_TRY(axpby(st, n, cplx(1.0 / hn, 0), K.w, 0.0, K.V + (int64_t)(j + 1) * n));
-            // previous rotations
-            for (int i = 0; i < j; i++) {
-                cplx a = H[i * restart + j], bb = H[(i + 1) * restart + j];
-                H[i * restart + j] = cs[i] * a + sn[i] * bb;
-                H[(i + 1) * restart + j] = -std::conj(sn[i]) * a + cs[i] * bb;
-            }
-            cplx a = H[j * restart + j], bb = H[(j + 1) * restart + j];
-            double den = std::sqrt(std::norm(a) + std::norm(bb));
-            if (std::abs(a) == 0.0) {
-                cs[j] = 0.0;
-                sn[j] = 1.0;
-            } else {
-                cs[j] = std::abs(a) / den;
-                sn[j] = (a / std::abs(a)) * std::conj(bb) / den;
-            }
-            H[j * restart + j] = cs[j] * a + sn[j] * bb;
-            H[(j + 1) * restart + j] = 0.0;
-            cplx gj = g[j];
-            g[j] = cs[j] * gj;
-            g[j + 1] = -std::conj(sn[j]) * gj;
+            SIE_TRY(dots(st, n, j + 1, K.V, n, K.w, K.part, h1));
+            k_gemv<<<nb(n), 256, 0, st>>>(n, j + 1, K.V, n, h1, -1.0, K.w);
+            SIE_TRY(dots(st, n, j + 1, K.V, n, K.w, K.part, h2));
+            k_gemv<<<nb(n), 256, 0, st>>>(n, j + 1, K.V, n, h2, -1.0, K.w);
+            SIE_TRY(dots(st, n, 1, K.w, n, K.w, K.part, wd));
+            k_gm_next<<<nb(std::max<int64_t>(n, j + 1)), 256, 0, st>>>(n, j, m, h1, h2, wd, K.w,
+                                                                       K.V + (int64_t)(j + 1) * n, H);
+            k_gm_givens<<<1, 1, 0, st>>>(j, m, H, cs, sn, g, K.sc);
+            SIE_CUDA_TRY(cudaGetLastError());
+            SIE_CUDA_TRY(cudaMemcpyAsync(K.resid_h + j, K.sc + 3 + j, sizeof(double), cudaMemcpyDeviceToHost, st));
+            SIE_CUDA_TRY(cudaEventRecord(K.ev[j], st));
             it++;
-            rel = std::abs(g[j + 1]) / bnorm;
-            if (rel < tol || it >= maxit || hn == 0.0) {
-                jend = j;
-                break;
+            if (j >= LAG) {
+                SIE_CUDA_TRY(cudaEventSynchronize(K.ev[j - LAG]));
+                if (K.resid_h[j - LAG] < tol) {
+                    conv = true;
+                    j++;
+                    break;
+                }
             }
         }
-        if (jend < 0) jend = restart - 1;
-        // back substitution
-        std::vector<cplx> y(jend + 1);
-        for (int i = jend; i >= 0; i--) {
-            cplx s = g[i];
-            for (int k2 = i + 1; k2 <= jend; k2++) s -= H[i * restart + k2] * y[k2];
-            y[i] = s / H[i * restart + i];
-        }
-        std::vector<double2> yd(jend + 1);
-        for (int i = 0; i <= jend; i++) yd[i] = make_double2(y[i].real(), y[i].imag());
-        SIE_CUDA_TRY(cudaMemcpyAsync(K.h, yd.data(), sizeof(double2) * (jend + 1), cudaMemcpyHostToDevice, st));
-        k_gemv<<<nb(n), 256, 0, st>>>(n, jend + 1, K.Z, n, K.h, 1.0, x);
+        const int jend = j - 1;
+        SIE_CUDA_TRY(cudaEventSynchronize(K.ev[jend]));
+        rel = K.resid_h[jend];
+        if (rel < tol) conv = true;
+        k_gm_backsub<<<1, 1, 0, st>>>(jend, m, H, g, y);
+        k_gemv<<<nb(n), 256, 0, st>>>(n, jend + 1, K.Z, n, y, 1.0, x);
         SIE_CUDA_TRY(cudaGetLastError());
-        SIE_CUDA_TRY(cudaStreamSynchronize(st));  // yd (pageable) consumed
-        if (rel < tol || it >= maxit) break;
-        // true residual for the restart
+        if (conv || it >= maxit) break;
+        // restart from the true residual
         SIE_TRY(A(x, K.w));
         SIE_CUDA_TRY(cudaMemcpyAsync(K.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
         SIE_TRY(axpby(st, n, -1.0, K.w, 1.0, K.r));
-        SIE_TRY(dev_norm(st, n, K.r, K.part, K.h, &beta));
-        rel = beta / bnorm;
+        SIE_TRY(dots(st, n, 1, K.r, n, K.r, K.part, wd));
+        k_gm_start<<<nb(n), 256, 0, st>>>(n, K.r, wd, K.V, g, m, K.sc, 0);
+        SIE_CUDA_TRY(cudaGetLastError());
+        SIE_CUDA_TRY(cudaMemcpyAsync(K.resid_h, K.sc + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        SIE_CUDA_TRY(cudaStreamSynchronize(st));
+        rel = K.resid_h[0] / bnorm;
         if (rel < tol) break;
     }
     if (iters_out) *iters_out = it;
