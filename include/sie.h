@@ -97,6 +97,7 @@ typedef struct {
                              (charge) system (1e-6)                                    */
     int constraint_maxit; /* ... and its iteration cap (1000)                          */
     int constraint_restart; /* ... and its GMRES restart length (100)                  */
+    double tol_constraint_inner; /* the same for the nested (interior) preconditioner (1e-3) */
     /* near-field quadrature (the method's direct-integration rule) */
     int q_far;            /* far-near pairs: q_far x q_far collapsed Gauss per triangle (5) */
     int q_out;            /* close pairs: q_out x q_out outer points (5)                */
@@ -156,7 +157,8 @@ sie_status sie_op_destroy(sie_op* op);
  * the system product: SIE_FP64 or SIE_MIXED = complex64 projection, FFT,
  * spectral multiply and interpolation with FP64 near-region products and
  * FP64 Krylov), tol_outer, tol_inner, maxit, restart, inner_maxit,
- * tol_constraint, constraint_maxit, constraint_restart are taken from params;
+ * tol_constraint, constraint_maxit, constraint_restart, tol_constraint_inner are
+ * taken from params;
  * grid and quadrature fields are ignored (they are fixed at build time). */
 sie_status sie_op_set_solver(sie_op* op, const sie_params* params);
 

@@ -40,7 +40,7 @@ class sie_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("tol_outer", ctypes.c_double), ("tol_inner", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("inner_maxit", ctypes.c_int),
                 ("tol_constraint", ctypes.c_double), ("constraint_maxit", ctypes.c_int),
-                ("constraint_restart", ctypes.c_int),
+                ("constraint_restart", ctypes.c_int), ("tol_constraint_inner", ctypes.c_double),
                 ("q_far", ctypes.c_int), ("q_out", ctypes.c_int), ("q_ang", ctypes.c_int), ("q_rad", ctypes.c_int),
                 ("q_npan", ctypes.c_int), ("q_opan", ctypes.c_int), ("q_olam", ctypes.c_int),
                 ("q_omu", ctypes.c_int), ("q_emupan", ctypes.c_int), ("q_emu", ctypes.c_int),

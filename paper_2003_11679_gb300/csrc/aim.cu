@@ -185,7 +185,8 @@ struct PassGeom {
 };
 
 // One CTA transforms PB pencils of length n = 2^LOGN held in shared memory.
-// Load at bit-reversed positions, log2(n) radix-2 DIT stages, store.
+// Load at bit-reversed positions, log2(n) radix-2 DIT stages (the first two
+// fused into one radix-4 pass without multiplications), store.
 template <class C>
 __device__ __forceinline__ C cmake(double a, double b);
 template <>
@@ -222,8 +223,46 @@ __global__ void __launch_bounds__(256) k_fft_pass(const C* in, C* out,  // may a
         sm[pl * pitch + (__brev(j) >> (32 - LOGN))] = v;
     }
     __syncthreads();
+    // stages 1 and 2 have trivial twiddles (1 and -+j): adds and swaps only
+    for (int q = threadIdx.x; q < PB * (n / 4); q += blockDim.x) {
+        int pl = q / (n / 4), base = 4 * (q % (n / 4));
+        C* p = sm + pl * pitch + base;
+        C x0 = p[0], x1 = p[1], x2 = p[2], x3 = p[3];
+        C a0, a1, b0, b1;
+        a0.x = x0.x + x1.x;
+        a0.y = x0.y + x1.y;
+        a1.x = x0.x - x1.x;
+        a1.y = x0.y - x1.y;
+        b0.x = x2.x + x3.x;
+        b0.y = x2.y + x3.y;
+        b1.x = x2.x - x3.x;
+        b1.y = x2.y - x3.y;
+        // stage 2: w = 1 for (a0, b0); w = -j (forward) or +j (inverse) for (a1, b1)
+        C t;
+        if (inv) {
+            t.x = -b1.y;
+            t.y = b1.x;
+        } else {
+            t.x = b1.y;
+            t.y = -b1.x;
+        }
+        C y0, y1, y2, y3;
+        y0.x = a0.x + b0.x;
+        y0.y = a0.y + b0.y;
+        y2.x = a0.x - b0.x;
+        y2.y = a0.y - b0.y;
+        y1.x = a1.x + t.x;
+        y1.y = a1.y + t.y;
+        y3.x = a1.x - t.x;
+        y3.y = a1.y - t.y;
+        p[0] = y0;
+        p[1] = y1;
+        p[2] = y2;
+        p[3] = y3;
+    }
+    __syncthreads();
 #pragma unroll 1
-    for (int s = 1; s <= LOGN; s++) {
+    for (int s = 3; s <= LOGN; s++) {
         const int half = 1 << (s - 1);
         for (int bfly = threadIdx.x; bfly < PB * (n / 2); bfly += blockDim.x) {
             int pl = bfly / (n / 2), bb = bfly % (n / 2);

@@ -414,6 +414,7 @@ void sie_params_default(sie_params* p)
     p->tol_constraint = 1e-6;
     p->constraint_maxit = 1000;
     p->constraint_restart = 100;
+    p->tol_constraint_inner = 1e-3;
     p->q_far = 5;
     p->q_out = 5;
     p->q_ang = 8;
@@ -566,6 +567,7 @@ sie_status sie_op_set_solver(sie_op* op, const sie_params* p)
     op->p.tol_constraint = p->tol_constraint;
     op->p.constraint_maxit = p->constraint_maxit;
     op->p.constraint_restart = p->constraint_restart;
+    if (p->tol_constraint_inner > 0) op->p.tol_constraint_inner = p->tol_constraint_inner;
     if (p->precision == SIE_FP64 || p->precision == SIE_MIXED) op->p.precision = p->precision;
     return SIE_OK;
 }

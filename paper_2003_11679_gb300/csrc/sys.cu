@@ -270,10 +270,9 @@ __global__ void k_gm_backsub(int jend, int m, const double2* __restrict__ H, con
 // monitored residual is the true residual of A x = b.  Arnoldi in FP64 with
 // classical Gram-Schmidt applied twice.  Everything stays on the device: the
 // Hessenberg column, the Givens rotations and the back substitution are tiny
-// kernels; the host reads each iteration's residual LAG iterations later
+// kernels; the host reads each iteration's residual one iteration later
 // (event on a pinned copy), so the GPU does not wait on host round trips.
-// Up to LAG extra iterations may run after convergence (they only lower the
-// residual).
+// One extra iteration may run after convergence (it only lowers the residual).
 static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, const Apply& Minv, const double2* b,
                          double2* x, double tol, int maxit, int restart, int* iters_out, double* relres_out)
 {
@@ -303,7 +302,7 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
         if (relres_out) *relres_out = 0.0;
         return SIE_OK;
     }
-    const int LAG = 2;
+    const int LAG = 1;
     while (true) {
         int j = 0;
         bool conv = false;
@@ -740,7 +739,8 @@ static GL8 gl_rule(int n)
 }
 
 // ------------------------------------------------------------------ operators
-static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork& K, const double2* v, double2* y);
+static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork& K, double tol, const double2* v,
+                                   double2* y);
 
 // interior impedance E' = Z' H = -(j k0 eps_r + sigma eta0)^-1 L_i^-1 (K_i - Ix/2) H
 static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_iters)
@@ -754,7 +754,23 @@ static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_i
     AimOp& I = op->inn;
     Apply A = [&](const double2* x, double2* y) { return aim_apply(op, I, 0, x, y); };
     cplx ki(I.kr, I.ki);
-    Apply Minv = [&](const double2* x, double2* y) { return constraint_solve(op, I, 1.0 / (ki * ki), op->kcs_in, x, y); };
+    // Nested preconditioner M_i of Eq. (nest2pc) in its near-region form: the
+    // constraint form (diag LA_i + near Lphi_i, block elimination) when the
+    // scalar-potential term matters, plain Jacobi on diag(L_i) when the object
+    // is near-region only (skin depth below the near region: |k_i| l >> 1 makes
+    // the k_i^-2 term negligible next to the diagonal)
+    Apply Minv;
+    if (I.has_grid) {
+        Minv = [&](const double2* x, double2* y) {
+            return constraint_solve(op, I, 1.0 / (ki * ki), op->kcs_in, op->p.tol_constraint_inner, x, y);
+        };
+    } else {
+        Minv = [&](const double2* x, double2* y) {
+            k_jacobi<<<nb(ne), 256, 0, st>>>(ne, x, I.dL, make_double2(1.0, 0.0), y);
+            SIE_CUDA_TRY(cudaGetLastError());
+            return SIE_OK;
+        };
+    }
     int it = 0;
     double rr = 0;
     sie_status s;
@@ -861,7 +877,8 @@ static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
 //     (I - kappa D Dg^-1 D^T Lphi_NR) q = D Dg^-1 v,   y = Dg^-1 (v + kappa D^T Lphi_NR q),
 // the triangle system solved by an inner GMRES to a loose tolerance (the
 // outer iterations are flexible).
-static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork& K, const double2* v, double2* y)
+static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork& K, double tol, const double2* v,
+                                   double2* y)
 {
     sie_ctx* c = op->mesh->ctx;
     cudaStream_t st = c->stream;
@@ -895,8 +912,7 @@ static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork&
     sie_status s;
     {
         Stage s_(c, "constraint_solve");
-        s = fgmres(c, K, nt, S, I, rq, q, op->p.tol_constraint, op->p.constraint_maxit, op->p.constraint_restart, &it,
-                   &rr);
+        s = fgmres(c, K, nt, S, I, rq, q, tol, op->p.constraint_maxit, op->p.constraint_restart, &it, &rr);
     }
     op->stats[4] = std::max(op->stats[4], (double)it);
     op->stats[5] = std::max(op->stats[5], rr);
@@ -936,7 +952,7 @@ static sie_status precond_sys(sie_op* op, const double2* x, double2* y)
     k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, ph, v1p);
     SIE_CUDA_TRY(cudaGetLastError());
     SIE_TRY(axpby(st, ne, 1.0, x, -1.0 / jk0, v1p));
-    SIE_TRY(constraint_solve(op, X, 1.0 / (op->k0 * op->k0), op->kcs_out, v1p, y));
+    SIE_TRY(constraint_solve(op, X, 1.0 / (op->k0 * op->k0), op->kcs_out, op->p.tol_constraint, v1p, y));
     SIE_TRY(axpby(st, ne, 1.0 / jk0, y, 0.0, y));
     // w2 = (v2 - F D w1) / (j k0), (F D w1)_t = (D w1)_t / A_t
     k_D<<<nb(nt), 256, 0, st>>>((int)nt, M, y, ph);
