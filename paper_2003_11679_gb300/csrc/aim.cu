@@ -6,6 +6,7 @@
 //   precorrected near-region CSR product (Eqs. LinNRP, KinNRP).
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -133,7 +134,7 @@ sie_status aim_weights(sie_op* op)
 }
 
 // ------------------------------------------------------------------ FFT
-// Twiddles exp(-2 pi i k / n), k < n/2, for n = 2^l (l <= 10), concatenated.
+// Twiddles exp(-2 pi i k / n), k < n, for n = 2^l (l <= 10).
 static double2* g_tw[11] = {nullptr};
 static float2* g_tw32[11] = {nullptr};
 static int g_tw_dev[11] = {-1};
@@ -147,8 +148,8 @@ static sie_status twiddles(int logn, cudaStream_t st, double2** out)
         return SIE_OK;
     }
     int n = 1 << logn;
-    std::vector<double2> h(std::max(n / 2, 1));
-    for (int k = 0; k < n / 2; k++) {
+    std::vector<double2> h(std::max(n, 1));
+    for (int k = 0; k < n; k++) {
         long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)n;
         h[k] = make_double2((double)cosl(a), (double)sinl(a));
     }
@@ -301,13 +302,223 @@ __global__ void __launch_bounds__(256) k_fft_pass(const C* in, C* out,  // may a
     }
 }
 
-template <int LOGN, class C>
-static sie_status launch_pass_n(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G)
+
+// ------------------------------------------------------------------ Stockham FFT (register radix-8)
+// Self-sorting Stockham formulation (Govindaraju et al., SC'08): pass p with
+// current span Ns and radix R: thread j loads a[r] = x[j + r n/R], multiplies
+// by exp(-+2 pi i (j mod Ns) r / (Ns R)), does an R-point DFT in registers and
+// stores y[(j / Ns) Ns R + (j mod Ns) + r Ns].  n/8 threads per pencil; the
+// first pass reads the (zero padded) pencil straight from global memory, the
+// last writes the (truncated) output straight to global memory, the passes in
+// between exchange through shared memory.
+template <class C, int INV>
+__device__ __forceinline__ void cmulw(C& a, C w)
+{
+    C t;
+    if (INV) w.y = -w.y;
+    t.x = a.x * w.x - a.y * w.y;
+    t.y = a.x * w.y + a.y * w.x;
+    a = t;
+}
+
+template <class C, int INV>
+__device__ __forceinline__ void bfly2(C& a, C& b)
+{
+    C t = a;
+    a.x = t.x + b.x;
+    a.y = t.y + b.y;
+    b.x = t.x - b.x;
+    b.y = t.y - b.y;
+}
+
+// multiply by -j (forward) or +j (inverse)
+template <class C, int INV>
+__device__ __forceinline__ C mulmj(C a)
+{
+    C t;
+    if (INV) {
+        t.x = -a.y;
+        t.y = a.x;
+    } else {
+        t.x = a.y;
+        t.y = -a.x;
+    }
+    return t;
+}
+
+template <class C, int INV>
+__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3)
+{
+    // X0 = (a0+a2)+(a1+a3), X2 = (a0+a2)-(a1+a3), X1 = (a0-a2) -+j (a1-a3), X3 = (a0-a2) +-j (a1-a3)
+    bfly2<C, INV>(a0, a2);
+    bfly2<C, INV>(a1, a3);
+    a3 = mulmj<C, INV>(a3);
+    bfly2<C, INV>(a0, a1);
+    bfly2<C, INV>(a2, a3);
+    // now a0 = X0, a1 = X2, a2 = X1, a3 = X3 -> reorder
+    C t = a1;
+    a1 = a2;
+    a2 = t;
+}
+
+template <class C, int INV>
+__device__ __forceinline__ void dft8(C* a)
+{
+    // even/odd split: E = DFT4(a0,a2,a4,a6), O = DFT4(a1,a3,a5,a7)
+    dft4<C, INV>(a[0], a[2], a[4], a[6]);
+    dft4<C, INV>(a[1], a[3], a[5], a[7]);
+    const double r = 0.70710678118654752440;
+    // O[k] *= W8^k : W8 = (1 -+ j)/sqrt2, W8^2 = -+j, W8^3 = (-1 -+ j)/sqrt2
+    C o1 = a[3], o2 = a[5], o3 = a[7];
+    C t;
+    if (!INV) {
+        t.x = (o1.x + o1.y) * r;
+        t.y = (o1.y - o1.x) * r;
+    } else {
+        t.x = (o1.x - o1.y) * r;
+        t.y = (o1.y + o1.x) * r;
+    }
+    o1 = t;
+    o2 = mulmj<C, INV>(o2);
+    if (!INV) {
+        t.x = (o3.y - o3.x) * r;
+        t.y = -(o3.x + o3.y) * r;
+    } else {
+        t.x = -(o3.x + o3.y) * r;
+        t.y = (o3.x - o3.y) * r;
+    }
+    o3 = t;
+    // E[k] in a[0], a[2], a[4], a[6]; O[k] (twiddled) in a[1], o1, o2, o3
+    C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6], q0 = a[1];
+    a[0].x = e0.x + q0.x; a[0].y = e0.y + q0.y;
+    a[4].x = e0.x - q0.x; a[4].y = e0.y - q0.y;
+    a[1].x = e1.x + o1.x; a[1].y = e1.y + o1.y;
+    a[5].x = e1.x - o1.x; a[5].y = e1.y - o1.y;
+    a[2].x = e2.x + o2.x; a[2].y = e2.y + o2.y;
+    a[6].x = e2.x - o2.x; a[6].y = e2.y - o2.y;
+    a[3].x = e3.x + o3.x; a[3].y = e3.y + o3.y;
+    a[7].x = e3.x - o3.x; a[7].y = e3.y - o3.y;
+}
+
+template <class C, int INV, int R>
+__device__ __forceinline__ void dftR(C* a)
+{
+    if constexpr (R == 8)
+        dft8<C, INV>(a);
+    else if constexpr (R == 4)
+        dft4<C, INV>(a[0], a[1], a[2], a[3]);
+    else
+        bfly2<C, INV>(a[0], a[1]);
+}
+
+// one Stockham pass of radix R over the pencil held by (tp = thread in pencil);
+// SRC / DST: 0 = global, 1 = shared memory
+template <int LOGN, int R, int SRC, int DST, class C, int INV>
+__device__ __forceinline__ void stockham_pass(int Ns, int tp, const C* gin, int64_t gbase_in, int64_t gst_in,
+                                              int n_in, C* gout, int64_t gbase_out, int64_t gst_out, int n_out,
+                                              bool valid, const C* sin, C* sout, const C* __restrict__ tw)
 {
     constexpr int n = 1 << LOGN;
-    constexpr int PB = (n >= 512) ? 8 : 16;
-    C* tw = nullptr;
-    SIE_TRY(twiddles(LOGN, st, &tw));
+    constexpr int TPP = n / 8;  // threads per pencil
+    constexpr int NB = n / R;   // butterflies per pencil
+    for (int jj = tp; jj < NB; jj += TPP) {
+        C a[R];
+        for (int r = 0; r < R; r++) {
+            int idx = jj + r * NB;
+            if (SRC == 0) {
+                C v;
+                v.x = 0;
+                v.y = 0;
+                if (valid && idx < n_in) v = gin[gbase_in + (int64_t)idx * gst_in];
+                a[r] = v;
+            } else {
+                a[r] = sin[idx];
+            }
+        }
+        int k = jj % Ns;
+        if (Ns > 1)
+            for (int r = 1; r < R; r++) cmulw<C, INV>(a[r], tw[(k * r) * (n / (Ns * R))]);
+        dftR<C, INV, R>(a);
+        int o = (jj / Ns) * Ns * R + k;
+        for (int r = 0; r < R; r++) {
+            int idx = o + r * Ns;
+            if (DST == 0) {
+                if (valid && idx < n_out) gout[gbase_out + (int64_t)idx * gst_out] = a[r];
+            } else {
+                sout[idx] = a[r];
+            }
+        }
+    }
+}
+
+template <int LOGN, int PB, class C, int INV>
+__global__ void __launch_bounds__(PB*(1 << LOGN) / 8) k_fft_stockham(const C* in, C* out, const C* __restrict__ tw,
+                                                                     PassGeom G)
+{
+    constexpr int n = 1 << LOGN;
+    constexpr int TPP = n / 8;
+    constexpr int pitch = n + 1;
+    extern __shared__ __align__(16) unsigned char smraw2[];
+    C* sm0 = reinterpret_cast<C*>(smraw2);
+    C* sm1 = sm0 + PB * pitch;
+    // pencil-fastest thread order on strided passes keeps rows coalesced
+    int pl, tp;
+    if (G.contig) {
+        pl = threadIdx.x / TPP;
+        tp = threadIdx.x % TPP;
+    } else {
+        pl = threadIdx.x % PB;
+        tp = threadIdx.x / PB;
+    }
+    int64_t p = (int64_t)blockIdx.x * PB + pl;
+    bool valid = p < G.npencil;
+    int64_t bin = valid ? (p % G.L) * G.slo_in + (p / G.L) * G.shi_in : 0;
+    int64_t bout = valid ? (p % G.L) * G.slo_out + (p / G.L) * G.shi_out : 0;
+    C* s0 = sm0 + pl * pitch;
+    C* s1 = sm1 + pl * pitch;
+    // radix plan: 8^a x (1, 2 or 4)
+    constexpr int NP8 = LOGN / 3, REM = LOGN % 3;
+    constexpr int NPASS = NP8 + (REM ? 1 : 0);
+    int Ns = 1;
+    // pass 0 (global -> smem or global)
+    if constexpr (NPASS == 1) {
+        stockham_pass<LOGN, 8, 0, 0, C, INV>(Ns, tp, in, bin, G.st_in, G.n_in, out, bout, G.st_out, G.n_out, valid,
+                                             nullptr, nullptr, tw);
+        return;
+    } else {
+        stockham_pass<LOGN, 8, 0, 1, C, INV>(Ns, tp, in, bin, G.st_in, G.n_in, nullptr, 0, 0, 0, valid, nullptr, s0,
+                                             tw);
+    }
+    Ns *= 8;
+    __syncthreads();
+    C* cur = s0;
+    C* nxt = s1;
+    for (int ps = 1; ps < NP8; ps++) {
+        bool last = (ps == NPASS - 1);
+        if (last) {
+            stockham_pass<LOGN, 8, 1, 0, C, INV>(Ns, tp, nullptr, 0, 0, 0, out, bout, G.st_out, G.n_out, valid, cur,
+                                                 nullptr, tw);
+            return;
+        }
+        stockham_pass<LOGN, 8, 1, 1, C, INV>(Ns, tp, nullptr, 0, 0, 0, nullptr, 0, 0, 0, valid, cur, nxt, tw);
+        Ns *= 8;
+        __syncthreads();
+        C* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if constexpr (REM == 1)
+        stockham_pass<LOGN, 2, 1, 0, C, INV>(Ns, tp, nullptr, 0, 0, 0, out, bout, G.st_out, G.n_out, valid, cur,
+                                             nullptr, tw);
+    else if constexpr (REM == 2)
+        stockham_pass<LOGN, 4, 1, 0, C, INV>(Ns, tp, nullptr, 0, 0, 0, out, bout, G.st_out, G.n_out, valid, cur,
+                                             nullptr, tw);
+}
+
+template <int LOGN, int PB, class C>
+static sie_status launch_pass_pb(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G, const C* tw)
+{
+    constexpr int n = 1 << LOGN;
     size_t smem = sizeof(C) * PB * (n + 1);
     static bool attr = false;
     if (!attr) {
@@ -318,6 +529,87 @@ static sie_status launch_pass_n(cudaStream_t st, const C* in, C* out, int inv, c
     k_fft_pass<LOGN, PB, C><<<blocks, 256, smem, st>>>(in, out, tw, inv, G);
     SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
+}
+
+// Pencils per CTA: as many as keep at least ~4 CTAs per SM in flight (more
+// pencils per CTA give longer coalesced rows on the strided passes, fewer
+// leave SMs idle on the small passes); SIE_FFT_PB overrides for tuning.
+static int pick_pb(int n, int64_t npencil)
+{
+    static int forced = -1;
+    if (forced < 0) {
+        const char* e = getenv("SIE_FFT_PB");
+        forced = e ? atoi(e) : 0;
+    }
+    if (forced == 4 || forced == 8 || forced == 16) return (n >= 512 && forced == 16) ? 8 : forced;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (!sms) sms = 152;
+    }
+    for (int pb : {16, 8, 4}) {
+        if (n >= 512 && pb == 16) continue;
+        if (npencil / pb >= 4LL * sms) return pb;
+    }
+    return 4;
+}
+
+template <int LOGN, int PB, class C>
+static sie_status launch_stockham(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G, const C* tw)
+{
+    constexpr int n = 1 << LOGN;
+    size_t smem = sizeof(C) * 2 * PB * (n + 1);
+    static bool attr = false;
+    if (!attr) {
+        SIE_CUDA_TRY(cudaFuncSetAttribute(k_fft_stockham<LOGN, PB, C, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        SIE_CUDA_TRY(cudaFuncSetAttribute(k_fft_stockham<LOGN, PB, C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        attr = true;
+    }
+    unsigned blocks = (unsigned)((G.npencil + PB - 1) / PB);
+    constexpr int threads = PB * n / 8;
+    if (inv)
+        k_fft_stockham<LOGN, PB, C, 1><<<blocks, threads, smem, st>>>(in, out, tw, G);
+    else
+        k_fft_stockham<LOGN, PB, C, 0><<<blocks, threads, smem, st>>>(in, out, tw, G);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+static int fft_kernel_choice()
+{
+    static int k = -1;
+    if (k < 0) {
+        const char* e = getenv("SIE_FFT_KERNEL");
+        k = (e && e[0] == 'r') ? 1 : 0;  // 0: Stockham radix-8 (default), 1: shared-memory radix-2
+    }
+    return k;
+}
+
+template <int LOGN, class C>
+static sie_status launch_pass_n(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G)
+{
+    C* tw = nullptr;
+    SIE_TRY(twiddles(LOGN, st, &tw));
+    if (fft_kernel_choice() == 0) {
+        // 256 threads per CTA (n/8 per pencil); halve the pencils per CTA when
+        // that leaves fewer than ~4 CTAs per SM
+        constexpr int PB = 2048 >> LOGN;
+        constexpr int PBh = PB >= 2 ? PB / 2 : 1;
+        int pb = pick_pb(1 << LOGN, G.npencil);
+        if (pb >= 16 || G.npencil / PB >= 4LL * 152) return launch_stockham<LOGN, PB, C>(st, in, out, inv, G, tw);
+        return launch_stockham<LOGN, PBh, C>(st, in, out, inv, G, tw);
+    }
+    switch (pick_pb(1 << LOGN, G.npencil)) {
+        case 16:
+            if constexpr (LOGN < 9) return launch_pass_pb<LOGN, 16, C>(st, in, out, inv, G, tw);
+            [[fallthrough]];
+        case 8: return launch_pass_pb<LOGN, 8, C>(st, in, out, inv, G, tw);
+        default: return launch_pass_pb<LOGN, 4, C>(st, in, out, inv, G, tw);
+    }
 }
 
 template <class C>
