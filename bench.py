@@ -123,6 +123,10 @@ def stage_model(stage, info, ne, nt, nnz_ext, nnz_int):
         "spmv_aim": (nnz_ext * (c + 4) + (ne + 1) * 8 + 3 * ne * c, 8.0 * nnz_ext),
         "spmv_near_only": (nnz_int * (c + 4) + (ne + 1) * 8 + 3 * ne * c, 8.0 * nnz_int),
         "specmul_sys": ((7 + 4 + 4) * nx * ny * nz * c, 8 * 10.0 * nx * ny * nz),
+        # two edge CSR products sharing the pattern (LA H and K E: 2 values + 1 col per nnz),
+        # Ix E (5 nnz/row), triangle Lphi product (info[7] pairs), vectors
+        "spmv_sys": (nnz_ext * (2 * c + 4) + 5 * ne * (c + 4) + int(info[7]) * (c + 4) + 8 * ne * c + 6 * nt * c,
+                     16.0 * nnz_ext + 8.0 * int(info[7])),
     }
     return table.get(stage)
 

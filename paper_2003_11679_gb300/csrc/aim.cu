@@ -183,6 +183,7 @@ struct PassGeom {
     int64_t slo_in, shi_in, st_in;
     int64_t slo_out, shi_out, st_out;
     int contig;            // 1: elements of a pencil are contiguous (x pass)
+    int64_t bs_in = 0, bs_out = 0;  // offsets between the grids of a batch (blockIdx.y)
 };
 
 // One CTA transforms PB pencils of length n = 2^LOGN held in shared memory.
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(const C* in, C* out,  // may a
         int64_t p = p0 + pl;
         C v = cmake<C>(0.0, 0.0);
         if (p < G.npencil && j < G.n_in) {
-            int64_t b = (p % G.L) * G.slo_in + (p / G.L) * G.shi_in;
+            int64_t b = (p % G.L) * G.slo_in + (p / G.L) * G.shi_in + blockIdx.y * G.bs_in;
             v = in[b + (int64_t)j * G.st_in];
         }
         sm[pl * pitch + (__brev(j) >> (32 - LOGN))] = v;
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(const C* in, C* out,  // may a
         }
         int64_t p = p0 + pl;
         if (p < G.npencil && j < G.n_out) {
-            int64_t b = (p % G.L) * G.slo_out + (p / G.L) * G.shi_out;
+            int64_t b = (p % G.L) * G.slo_out + (p / G.L) * G.shi_out + blockIdx.y * G.bs_out;
             out[b + (int64_t)j * G.st_out] = sm[pl * pitch + j];
         }
     }
@@ -472,8 +473,8 @@ __global__ void __launch_bounds__(PB*(1 << LOGN) / 8) k_fft_stockham(const C* in
     }
     int64_t p = (int64_t)blockIdx.x * PB + pl;
     bool valid = p < G.npencil;
-    int64_t bin = valid ? (p % G.L) * G.slo_in + (p / G.L) * G.shi_in : 0;
-    int64_t bout = valid ? (p % G.L) * G.slo_out + (p / G.L) * G.shi_out : 0;
+    int64_t bin = valid ? (p % G.L) * G.slo_in + (p / G.L) * G.shi_in + blockIdx.y * G.bs_in : 0;
+    int64_t bout = valid ? (p % G.L) * G.slo_out + (p / G.L) * G.shi_out + blockIdx.y * G.bs_out : 0;
     C* s0 = sm0 + pl * pitch;
     C* s1 = sm1 + pl * pitch;
     // radix plan: 8^a x (1, 2 or 4)
@@ -516,7 +517,8 @@ __global__ void __launch_bounds__(PB*(1 << LOGN) / 8) k_fft_stockham(const C* in
 }
 
 template <int LOGN, int PB, class C>
-static sie_status launch_pass_pb(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G, const C* tw)
+static sie_status launch_pass_pb(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G, const C* tw,
+                                 int nbatch)
 {
     constexpr int n = 1 << LOGN;
     size_t smem = sizeof(C) * PB * (n + 1);
@@ -526,7 +528,7 @@ static sie_status launch_pass_pb(cudaStream_t st, const C* in, C* out, int inv, 
         attr = true;
     }
     unsigned blocks = (unsigned)((G.npencil + PB - 1) / PB);
-    k_fft_pass<LOGN, PB, C><<<blocks, 256, smem, st>>>(in, out, tw, inv, G);
+    k_fft_pass<LOGN, PB, C><<<dim3(blocks, nbatch), 256, smem, st>>>(in, out, tw, inv, G);
     SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
 }
@@ -557,7 +559,8 @@ static int pick_pb(int n, int64_t npencil)
 }
 
 template <int LOGN, int PB, class C>
-static sie_status launch_stockham(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G, const C* tw)
+static sie_status launch_stockham(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G, const C* tw,
+                                  int nbatch)
 {
     constexpr int n = 1 << LOGN;
     size_t smem = sizeof(C) * 2 * PB * (n + 1);
@@ -572,9 +575,9 @@ static sie_status launch_stockham(cudaStream_t st, const C* in, C* out, int inv,
     unsigned blocks = (unsigned)((G.npencil + PB - 1) / PB);
     constexpr int threads = PB * n / 8;
     if (inv)
-        k_fft_stockham<LOGN, PB, C, 1><<<blocks, threads, smem, st>>>(in, out, tw, G);
+        k_fft_stockham<LOGN, PB, C, 1><<<dim3(blocks, nbatch), threads, smem, st>>>(in, out, tw, G);
     else
-        k_fft_stockham<LOGN, PB, C, 0><<<blocks, threads, smem, st>>>(in, out, tw, G);
+        k_fft_stockham<LOGN, PB, C, 0><<<dim3(blocks, nbatch), threads, smem, st>>>(in, out, tw, G);
     SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
 }
@@ -590,7 +593,7 @@ static int fft_kernel_choice()
 }
 
 template <int LOGN, class C>
-static sie_status launch_pass_n(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G)
+static sie_status launch_pass_n(cudaStream_t st, const C* in, C* out, int inv, const PassGeom& G, int nbatch)
 {
     C* tw = nullptr;
     SIE_TRY(twiddles(LOGN, st, &tw));
@@ -599,30 +602,31 @@ static sie_status launch_pass_n(cudaStream_t st, const C* in, C* out, int inv, c
         // that leaves fewer than ~4 CTAs per SM
         constexpr int PB = 2048 >> LOGN;
         constexpr int PBh = PB >= 2 ? PB / 2 : 1;
-        int pb = pick_pb(1 << LOGN, G.npencil);
-        if (pb >= 16 || G.npencil / PB >= 4LL * 152) return launch_stockham<LOGN, PB, C>(st, in, out, inv, G, tw);
-        return launch_stockham<LOGN, PBh, C>(st, in, out, inv, G, tw);
+        int pb = pick_pb(1 << LOGN, G.npencil * nbatch);
+        if (pb >= 16 || G.npencil * nbatch / PB >= 4LL * 152)
+            return launch_stockham<LOGN, PB, C>(st, in, out, inv, G, tw, nbatch);
+        return launch_stockham<LOGN, PBh, C>(st, in, out, inv, G, tw, nbatch);
     }
-    switch (pick_pb(1 << LOGN, G.npencil)) {
+    switch (pick_pb(1 << LOGN, G.npencil * nbatch)) {
         case 16:
-            if constexpr (LOGN < 9) return launch_pass_pb<LOGN, 16, C>(st, in, out, inv, G, tw);
+            if constexpr (LOGN < 9) return launch_pass_pb<LOGN, 16, C>(st, in, out, inv, G, tw, nbatch);
             [[fallthrough]];
-        case 8: return launch_pass_pb<LOGN, 8, C>(st, in, out, inv, G, tw);
-        default: return launch_pass_pb<LOGN, 4, C>(st, in, out, inv, G, tw);
+        case 8: return launch_pass_pb<LOGN, 8, C>(st, in, out, inv, G, tw, nbatch);
+        default: return launch_pass_pb<LOGN, 4, C>(st, in, out, inv, G, tw, nbatch);
     }
 }
 
 template <class C>
-static sie_status launch_pass(cudaStream_t st, int n, const C* in, C* out, int inv, const PassGeom& G)
+static sie_status launch_pass(cudaStream_t st, int n, const C* in, C* out, int inv, const PassGeom& G, int nb = 1)
 {
     switch (n) {
-        case 16: return launch_pass_n<4>(st, in, out, inv, G);
-        case 32: return launch_pass_n<5>(st, in, out, inv, G);
-        case 64: return launch_pass_n<6>(st, in, out, inv, G);
-        case 128: return launch_pass_n<7>(st, in, out, inv, G);
-        case 256: return launch_pass_n<8>(st, in, out, inv, G);
-        case 512: return launch_pass_n<9>(st, in, out, inv, G);
-        case 1024: return launch_pass_n<10>(st, in, out, inv, G);
+        case 16: return launch_pass_n<4>(st, in, out, inv, G, nb);
+        case 32: return launch_pass_n<5>(st, in, out, inv, G, nb);
+        case 64: return launch_pass_n<6>(st, in, out, inv, G, nb);
+        case 128: return launch_pass_n<7>(st, in, out, inv, G, nb);
+        case 256: return launch_pass_n<8>(st, in, out, inv, G, nb);
+        case 512: return launch_pass_n<9>(st, in, out, inv, G, nb);
+        case 1024: return launch_pass_n<10>(st, in, out, inv, G, nb);
     }
     set_error("unsupported FFT length");
     return SIE_ERR_UNSUPPORTED;
@@ -632,60 +636,67 @@ static sie_status launch_pass(cudaStream_t st, int n, const C* in, C* out, int i
 // full n grid already in buf) into the full spectrum in buf.
 // dir = +1: inverse of the spectrum in buf; prune = 1 writes only the physical
 // N box into the compact array `src` (used as output), prune = 0 keeps n^3 in buf.
+// nbatch grids at once: grid k at buf + k n^3 and (compact) src + k N^3
 template <class C>
-static sie_status fft3d_t(cudaStream_t st, C* buf, const C* src, const GridDesc& g, int dir, int prune, sie_ctx* pc)
+static sie_status fft3d_t(cudaStream_t st, C* buf, const C* src, const GridDesc& g, int dir, int prune, sie_ctx* pc,
+                          int nbatch)
 {
     const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int64_t Nx = prune ? g.N[0] : nx, Ny = prune ? g.N[1] : ny, Nz = prune ? g.N[2] : nz;
     const int64_t pyz = nx * ny;  // padded plane
+    const int64_t bnn = nx * ny * nz, bNg = (int64_t)g.N[0] * g.N[1] * g.N[2];
     if (dir < 0) {
         // x pass: pencils (y < Ny, z < Nz)
-        PassGeom X{(int)Nx, (int)nx, Ny * Nz, (int)Ny, prune ? Nx : nx, prune ? Nx * Ny : pyz, 1, nx, pyz, 1, 1};
+        PassGeom X{(int)Nx, (int)nx, Ny * Nz, (int)Ny, prune ? Nx : nx, prune ? Nx * Ny : pyz, 1, nx, pyz, 1, 1,
+                   prune ? bNg : bnn, bnn};
         {
             Stage s_(pc, "fft_fwd_x");
-            SIE_TRY(launch_pass(st, (int)nx, prune ? src : buf, buf, 0, X));
+            SIE_TRY(launch_pass(st, (int)nx, prune ? src : buf, buf, 0, X, nbatch));
         }
         // y pass: pencils (x < nx, z < Nz)
-        PassGeom Y{(int)Ny, (int)ny, nx * Nz, (int)nx, 1, pyz, nx, 1, pyz, nx, 0};
+        PassGeom Y{(int)Ny, (int)ny, nx * Nz, (int)nx, 1, pyz, nx, 1, pyz, nx, 0, bnn, bnn};
         {
             Stage s_(pc, "fft_fwd_y");
-            SIE_TRY(launch_pass(st, (int)ny, buf, buf, 0, Y));
+            SIE_TRY(launch_pass(st, (int)ny, buf, buf, 0, Y, nbatch));
         }
         // z pass: pencils (x < nx, y < ny)
-        PassGeom Z{(int)Nz, (int)nz, nx * ny, (int)nx, 1, nx, pyz, 1, nx, pyz, 0};
+        PassGeom Z{(int)Nz, (int)nz, nx * ny, (int)nx, 1, nx, pyz, 1, nx, pyz, 0, bnn, bnn};
         {
             Stage s_(pc, "fft_fwd_z");
-            SIE_TRY(launch_pass(st, (int)nz, buf, buf, 0, Z));
+            SIE_TRY(launch_pass(st, (int)nz, buf, buf, 0, Z, nbatch));
         }
     } else {
-        PassGeom Z{(int)nz, (int)Nz, nx * ny, (int)nx, 1, nx, pyz, 1, nx, pyz, 0};
+        PassGeom Z{(int)nz, (int)Nz, nx * ny, (int)nx, 1, nx, pyz, 1, nx, pyz, 0, bnn, bnn};
         {
             Stage s_(pc, "fft_inv_z");
-            SIE_TRY(launch_pass(st, (int)nz, buf, buf, 1, Z));
+            SIE_TRY(launch_pass(st, (int)nz, buf, buf, 1, Z, nbatch));
         }
-        PassGeom Y{(int)ny, (int)Ny, nx * Nz, (int)nx, 1, pyz, nx, 1, pyz, nx, 0};
+        PassGeom Y{(int)ny, (int)Ny, nx * Nz, (int)nx, 1, pyz, nx, 1, pyz, nx, 0, bnn, bnn};
         {
             Stage s_(pc, "fft_inv_y");
-            SIE_TRY(launch_pass(st, (int)ny, buf, buf, 1, Y));
+            SIE_TRY(launch_pass(st, (int)ny, buf, buf, 1, Y, nbatch));
         }
         C* dst = prune ? const_cast<C*>(src) : buf;
-        PassGeom X{(int)nx, (int)Nx, Ny * Nz, (int)Ny, nx, pyz, 1, prune ? Nx : nx, prune ? Nx * Ny : pyz, 1, 1};
+        PassGeom X{(int)nx, (int)Nx, Ny * Nz, (int)Ny, nx, pyz, 1, prune ? Nx : nx, prune ? Nx * Ny : pyz, 1, 1,
+                   bnn, prune ? bNg : bnn};
         {
             Stage s_(pc, "fft_inv_x");
-            SIE_TRY(launch_pass(st, (int)nx, buf, dst, 1, X));
+            SIE_TRY(launch_pass(st, (int)nx, buf, dst, 1, X, nbatch));
         }
     }
     return SIE_OK;
 }
 
-sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune, sie_ctx* pc)
+sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune, sie_ctx* pc,
+                 int nbatch)
 {
-    return fft3d_t(st, buf, src, g, dir, prune, pc);
+    return fft3d_t(st, buf, src, g, dir, prune, pc, nbatch);
 }
 
-sie_status fft3d(cudaStream_t st, float2* buf, const float2* src, const GridDesc& g, int dir, int prune, sie_ctx* pc)
+sie_status fft3d(cudaStream_t st, float2* buf, const float2* src, const GridDesc& g, int dir, int prune, sie_ctx* pc,
+                 int nbatch)
 {
-    return fft3d_t(st, buf, src, g, dir, prune, pc);
+    return fft3d_t(st, buf, src, g, dir, prune, pc, nbatch);
 }
 
 // ------------------------------------------------------------------ kernel spectra
@@ -748,7 +759,7 @@ sie_status aim_spectra(sie_op* op, AimOp& a)
     SIE_CUDA_TRY(cudaMallocAsync((void**)&a.spec, sizeof(double2) * 4 * nn, st));
     k_sample<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(g, a.kr, a.ki, a.spec, nn);
     SIE_CUDA_TRY(cudaGetLastError());
-    for (int c = 0; c < 4; c++) SIE_TRY(fft3d(st, a.spec + c * nn, (const double2*)nullptr, g, -1, 0, nullptr));
+    SIE_TRY(fft3d(st, a.spec, (const double2*)nullptr, g, -1, 0, nullptr, 4));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&a.spec32, sizeof(float2) * 4 * nn, st));
     k_to_c64<<<(unsigned)((4 * nn + 255) / 256), 256, 0, st>>>(a.spec, a.spec32, 4 * nn);
     SIE_CUDA_TRY(cudaGetLastError());
@@ -887,14 +898,32 @@ __global__ void k_interp(int nt, int S, int Mord, DevMesh M, const int32_t* __re
 
 // ------------------------------------------------------------------ near CSR product
 // y[m] += sum_e val[e] x[col[e]]; one warp per row
-__global__ void k_spmv(int nrow, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                       const double2* __restrict__ val, const double2* __restrict__ x, double2* __restrict__ y)
+__global__ void __launch_bounds__(128) k_spmv(int nrow, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                              const double2* __restrict__ val, const double2* __restrict__ x,
+                                              double2* __restrict__ y)
 {
     int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (r >= nrow) return;
     double ar = 0, ai = 0;
-    for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += 32) {
+    const int64_t e1 = rp[r + 1];
+    int64_t e = rp[r] + lane;
+    for (; e + 96 < e1; e += 128) {  // 4 independent loads per lane in flight
+        int c[4];
+        double2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            c[u] = __ldg(col + e + 32 * u);
+            v[u] = __ldg(val + e + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            double2 xv = __ldg(x + c[u]);
+            ar += v[u].x * xv.x - v[u].y * xv.y;
+            ai += v[u].x * xv.y + v[u].y * xv.x;
+        }
+    }
+    for (; e < e1; e += 32) {
         double2 v = val[e], xv = x[col[e]];
         ar += v.x * xv.x - v.y * xv.y;
         ai += v.x * xv.y + v.y * xv.x;
@@ -943,13 +972,13 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
             k_project<<<(M.nt * S + 255) / 256, 256, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, x, g, ngrid, src, Ng);
             SIE_CUDA_TRY(cudaGetLastError());
         }
-        for (int c = 0; c < ngrid; c++) SIE_TRY(fft3d(st, buf + c * nn, src + c * Ng, g, -1, 1, pc));
+        SIE_TRY(fft3d(st, buf, src, g, -1, 1, pc, ngrid));
         {
             Stage s_(pc, "specmul");
             k_specmul<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(which_LK, a.spec, buf, nn);
             SIE_CUDA_TRY(cudaGetLastError());
         }
-        for (int c = 0; c < ngrid; c++) SIE_TRY(fft3d(st, buf + c * nn, src + c * Ng, g, +1, 1, pc));
+        SIE_TRY(fft3d(st, buf, src, g, +1, 1, pc, ngrid));
         std::complex<double> kk(a.kr, a.ki);
         std::complex<double> sc = -1.0 / (kk * kk);
         {
