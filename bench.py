@@ -106,7 +106,8 @@ def measured_peaks():
 def stage_model(stage, info, ne, nt, nnz_ext, nnz_int):
     """Algorithmic bytes and FLOPs of ONE launch of a stage (FP64 complex = 16 B).
     FFT passes: one read of the pencils' live input and one write of the
-    output, 5 n log2 n flops per pencil (radix-2 operation count)."""
+    output, 5 n log2 n flops per pencil (radix-2 operation count), times the
+    grids one launch transforms (FFT_GRIDS)."""
     N = info[0:3].astype(np.int64)
     n = info[3:6].astype(np.int64)
     Nx, Ny, Nz = N
@@ -128,8 +129,14 @@ def stage_model(stage, info, ne, nt, nnz_ext, nnz_int):
         "spmv_sys": (nnz_ext * (2 * c + 4) + 5 * ne * (c + 4) + int(info[7]) * (c + 4) + 8 * ne * c + 6 * nt * c,
                      16.0 * nnz_ext + 8.0 * int(info[7])),
     }
-    return table.get(stage)
+    r = table.get(stage)
+    if r is not None and stage in FFT_GRIDS:
+        r = (r[0] * FFT_GRIDS[stage], r[1] * FFT_GRIDS[stage])
+    return r
 
+
+# grids per FFT launch in the system product: 7 forward (H, E, rho sources), 4 inverse
+FFT_GRIDS = {"fft_fwd_x": 7, "fft_fwd_y": 7, "fft_fwd_z": 7, "fft_inv_z": 4, "fft_inv_y": 4, "fft_inv_x": 4}
 
 FP64_PEAK_TFLOPS = 1.20  # measured FMA throughput (profiles/fp64_fma_peak_gb300.md); nominal 1.25
 
@@ -287,7 +294,7 @@ def mixed_line(ne, args, ms32, prof, err, info, peaks, kind):
     roof = None
     if kern:
         dom = max(kern, key=lambda k: kern[k][0])
-        B = model[dom]
+        B = model[dom] * FFT_GRIDS.get(dom, 1)
         avg = kern[dom][0] * 1e-3 / kern[dom][1]
         roof = {"bound": "hbm", "kernel": dom, "achieved": B / avg / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": B / avg / 1e9 / peaks["hbm_gbs"], "traffic": None, "peak_note": f"HBM copy, {kind}",
