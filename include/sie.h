@@ -207,6 +207,35 @@ sie_status sie_solve(sie_op* op, const double* b, double* x, int nrhs, int* iter
  * 4 pi |E_s|^2 r^2.  rcs: ndir doubles (host).  One right-hand side. */
 sie_status sie_rcs(sie_op* op, const double* x, const double* rhat, int ndir, double* rcs, int flags);
 
+/* Directions per sie_rcs_static call (bounds its static device array). */
+#define SIE_RCS_STATIC_MAX_DIR 2048
+
+/* sie_rcs that allocates nothing.  The paper has no counterpart: this is an
+ * interface variant of sie_rcs for callers that must not allocate once they
+ * run, such as a serving loop that reserves its device-memory budget at
+ * start-up and cannot let a request fail on out-of-memory or wait on the
+ * allocator.  sie_rcs allocates device scratch (directions, far-field sums)
+ * and a host staging array on every call; this variant keeps both in one
+ * statically sized device array of the library (SIE_RCS_STATIC_MAX_DIR x 17
+ * doubles, 272 KiB, one copy per device) and forms the cross sections on the
+ * device.  Arguments, layouts and results are those of sie_rcs (same
+ * far-field kernel and formula); ndir outside 1..SIE_RCS_STATIC_MAX_DIR
+ * returns SIE_ERR_ARG.
+ * Preconditions, else SIE_ERR_STATE with nothing launched: the operator has
+ * already run sie_solve or a SIE_OP_SYS/SIE_OP_ZI product with its current
+ * solver settings, so that the nested interior solve of Z' finds its Krylov
+ * workspaces at their sizes (sie_rcs would allocate them), and profiling
+ * (sie_profile_enable) is off, since its stage records grow host arrays.
+ * Set-up: the first call on each device looks up the array's address with
+ * cudaGetSymbolAddress, that device current, and caches it; make that first
+ * call before any stream capture begins on the device.
+ * Sharing: all calls on one device use the same array, so calls that overlap
+ * in time on a device (from other threads, streams or contexts) race on it;
+ * the caller serialises them.  Each call returns once its results are on the
+ * host.  No part of the array has to start at zero: a call writes every
+ * direction, far-field sum and cross section that it reads back. */
+sie_status sie_rcs_static(sie_op* op, const double* x, const double* rhat, int ndir, double* rcs, int flags);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,7 @@ SIE_OK = 0
 SIE_ERR_NOT_CONVERGED = 5
 SIE_FP64, SIE_MIXED = 0, 1
 SIE_DEVICE_PTRS = 1
+SIE_RCS_STATIC_MAX_DIR = 2048
 SIE_OP_L0, SIE_OP_K0, SIE_OP_LI, SIE_OP_KI, SIE_OP_SYS, SIE_OP_ZI = range(6)
 
 _STATUS = {0: "SIE_OK", 1: "SIE_ERR_ARG", 2: "SIE_ERR_MESH", 3: "SIE_ERR_OOM", 4: "SIE_ERR_CUDA",
@@ -31,7 +32,7 @@ SYMBOLS = ["sie_params_default", "sie_ctx_create", "sie_ctx_destroy", "sie_last_
            "sie_profile_read", "sie_mesh_create",
            "sie_mesh_destroy", "sie_mesh_counts", "sie_op_build", "sie_op_destroy", "sie_op_set_solver",
            "sie_op_stats", "sie_op_info", "sie_op_grid",
-           "sie_matvec", "sie_op_near_csr", "sie_rhs_planewave", "sie_solve", "sie_rcs"]
+           "sie_matvec", "sie_op_near_csr", "sie_rhs_planewave", "sie_solve", "sie_rcs", "sie_rcs_static"]
 
 
 class sie_params(ctypes.Structure):
@@ -84,6 +85,7 @@ def lib():
         L.sie_rhs_planewave.argtypes = [P, P, P, I, P, I]
         L.sie_solve.argtypes = [P, P, P, I, P, P, I]
         L.sie_rcs.argtypes = [P, P, P, I, P, I]
+        L.sie_rcs_static.argtypes = [P, P, P, I, P, I]
         for name in SYMBOLS:
             f = getattr(L, name)
             if name not in ("sie_params_default", "sie_last_error"):
@@ -251,6 +253,19 @@ class Operator:
         out = np.zeros(len(rh))
         px, dx = _ptr(x)
         _check(lib().sie_rcs(self.h, px, rh.ctypes.data, len(rh), out.ctypes.data, SIE_DEVICE_PTRS if dx else 0))
+        return out
+
+    def rcs_static(self, x, rhat):
+        """rcs() through sie_rcs_static, which allocates nothing (its scratch is a
+        fixed device array of the library): for callers that must not allocate
+        after start-up.  Needs a prior solve (or SYS product) on this operator and
+        profiling off; at most SIE_RCS_STATIC_MAX_DIR directions; calls that
+        overlap in time on one device race on the shared array."""
+        rh = np.ascontiguousarray(np.atleast_2d(rhat), dtype=np.float64)
+        out = np.zeros(len(rh))
+        px, dx = _ptr(x)
+        _check(lib().sie_rcs_static(self.h, px, rh.ctypes.data, len(rh), out.ctypes.data,
+                                    SIE_DEVICE_PTRS if dx else 0))
         return out
 
     def close(self):

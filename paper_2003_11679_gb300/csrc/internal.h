@@ -236,6 +236,9 @@ sie_status sys_matvec(sie_op* op, int which, const double2* x, double2* y);
 sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres);
 sie_status sys_rhs(sie_op* op, const double* khat, const double* epol, double2* b);
 sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, double* rcs);
+bool sys_z_workspace_ready(const sie_op* op);
+sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int ndir, double2* sums);
+double sys_rcs_scale(const sie_op* op);
 // nbatch consecutive grids (buf + k n^3, src + k N^3) in one launch per pass
 sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune,
                  sie_ctx* prof_ctx, int nbatch = 1);

@@ -1177,4 +1177,30 @@ sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, d
     return SIE_OK;
 }
 
+// True when Z' H can run without allocating: the interior FGMRES workspace (and,
+// for an interior on the AIM grid, the nested constraint solver's) already has
+// the sizes the solves use, as after a solve or a SYS product on this operator.
+bool sys_z_workspace_ready(const sie_op* op)
+{
+    const int64_t ne = op->mesh->h.ne, nt = op->mesh->h.nt;
+    if (op->kin.n != ne || op->kin.m != std::min(op->p.restart, 60)) return false;
+    if (op->inn.has_grid && (op->kcs_in.n != nt || op->kcs_in.m != op->p.constraint_restart)) return false;
+    return true;
+}
+
+// E' = Z' x[0:ne] into op->sys_E, then the far-field sums N(H), N(E') of the
+// directions rhat_d (device, 3 doubles each) into sums (device, 6 complex per
+// direction): the device half of sys_rcs, with caller-owned buffers.
+sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int ndir, double2* sums)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    SIE_TRY(apply_Z(op, x, op->sys_E, nullptr));
+    k_far<<<ndir, 256, 0, st>>>(op->mesh->d.nt, op->mesh->d, gl_rule(6), op->k0, rhat_d, x, op->sys_E, sums);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+// k0^2 eta0^2 / (4 pi): sigma = scale |N_perp(H) + rhat x N(E')|^2
+double sys_rcs_scale(const sie_op* op) { return op->k0 * op->k0 * ETA0 * ETA0 / (4 * M_PI); }
+
 }  // namespace sie
