@@ -938,6 +938,15 @@ __global__ void __launch_bounds__(128) k_spmv(int nrow, const int64_t* __restric
     }
 }
 
+sie_status csr_mv(cudaStream_t st, int nrow, const int64_t* rp, const int32_t* col, const double2* val,
+                  const double2* x, double2* y)
+{
+    SIE_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double2) * nrow, st));
+    k_spmv<<<(nrow + 3) / 4, 128, 0, st>>>(nrow, rp, col, val, x, y);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
 // y += W applied to the inverse-transformed grids (3 vector grids, + scalar grid)
 sie_status aim_interp(sie_op* op, const double2* grids, int has_phi, double2 scal, double2* y)
 {
@@ -997,10 +1006,10 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
 static void free_aim(AimOp& a)
 {
     void* ptrs[] = {a.spec, a.spec32, a.pairs, a.row_ptr, a.col, a.valL, a.valK, a.valLA, a.dLA, a.dL,
-                    a.tri_row_ptr, a.tri_col, a.valLphi, a.valLphiNR};
+                    a.tri_row_ptr, a.tri_col, a.valLphi, a.valLphiNR, a.valM};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    a.valLA = a.dLA = a.dL = a.valLphi = a.valLphiNR = nullptr;
+    a.valLA = a.dLA = a.dL = a.valLphi = a.valLphiNR = a.valM = nullptr;
     a.tri_row_ptr = nullptr;
     a.tri_col = nullptr;
     a.spec = nullptr;
@@ -1114,6 +1123,9 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
     }
     auto t4 = now();
     if ((s = near_build(op, op->inn, q)) != SIE_OK) return fail(s);
+    // near-only interior: approximate inverse of L_i,NR for the nested solve
+    if (!op->inn.has_grid && (s = spai_build(st, op->inn.csr, op->inn.valL, &op->inn.valM)) != SIE_OK)
+        return fail(s);
     op->build_ms[2] = ms(t4, now());
     // workspace
     int64_t nn = (int64_t)g.n[0] * g.n[1] * g.n[2], Ng = (int64_t)g.N[0] * g.N[1] * g.N[2];

@@ -79,6 +79,10 @@ void edge_csr_pattern(const HostMesh& m, const std::vector<int32_t>& pairs, CsrP
 // Gauss-Legendre on [0, 1] by Newton iteration on the Legendre recurrence
 void gauss_legendre01(int n, double* x, double* w);
 
+// sparse approximate inverse (pattern of P) of the device CSR values dval;
+// result allocated on the device in *dM
+sie_status spai_build(cudaStream_t st, const CsrPattern& P, const double2* dval, double2** dM);
+
 // ------------------------------------------------------------------ device data
 struct DevMesh {
     int nt = 0, ne = 0, nv = 0;
@@ -130,6 +134,7 @@ struct AimOp {
     int32_t* tri_col = nullptr;
     double2* valLphi = nullptr;
     double2* valLphiNR = nullptr;   // exact near Lphi (constraint preconditioner)
+    double2* valM = nullptr;        // sparse approximate inverse of valL (near-only interiors)
 };
 
 struct Workspace {
@@ -235,6 +240,9 @@ void sys_release(sie_op* op);
 sie_status sys_matvec(sie_op* op, int which, const double2* x, double2* y);
 sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres);
 sie_status sys_rhs(sie_op* op, const double* khat, const double* epol, double2* b);
+// y = A x for an edge CSR matrix (overwrites y)
+sie_status csr_mv(cudaStream_t st, int nrow, const int64_t* rp, const int32_t* col, const double2* val,
+                  const double2* x, double2* y);
 sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, double* rcs);
 bool sys_z_workspace_ready(const sie_op* op);
 sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int ndir, double2* sums);

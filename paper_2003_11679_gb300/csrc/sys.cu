@@ -826,9 +826,9 @@ static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_i
     cplx ki(I.kr, I.ki);
     // Nested preconditioner M_i of Eq. (nest2pc) in its near-region form: the
     // constraint form (diag LA_i + near Lphi_i, block elimination) when the
-    // scalar-potential term matters, plain Jacobi on diag(L_i) when the object
-    // is near-region only (skin depth below the near region: |k_i| l >> 1 makes
-    // the k_i^-2 term negligible next to the diagonal)
+    // object has an interior grid, and when it is near-region only (skin depth
+    // below the near region, L_i = L_i,NR) a sparse approximate inverse of
+    // L_i,NR on its own pattern, applied as one CSR product
     Apply Minv;
     if (I.has_grid) {
         Minv = [&](const double2* x, double2* y) {
@@ -836,9 +836,8 @@ static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_i
         };
     } else {
         Minv = [&](const double2* x, double2* y) {
-            k_jacobi<<<nb(ne), 256, 0, st>>>(ne, x, I.dL, make_double2(1.0, 0.0), y);
-            SIE_CUDA_TRY(cudaGetLastError());
-            return SIE_OK;
+            Stage s_(c, "spai_apply");
+            return csr_mv(st, (int)ne, I.row_ptr, I.col, I.valM, x, y);
         };
     }
     int it = 0;
