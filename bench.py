@@ -182,22 +182,28 @@ def run_ours(args):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
 
-        def timed(profile):
+        def timed(profile, label="timed"):
             """K steps, L2 flushed between them (outside the events); with
-            profile=True the library's per-stage CUDA events are recorded too."""
+            profile=True the library's per-stage CUDA events are recorded too.
+            The unprofiled loop sits in an NVTX range named `label` (for ncu
+            --nvtx-include)."""
             ctx.profile(profile)
+            if not profile:
+                torch.cuda.nvtx.range_push(label)
             for i in range(args.steps):
                 flush.fill_(float(i))
                 starts[i].record(stream)
                 step()
                 ends[i].record(stream)
             torch.cuda.synchronize()
+            if not profile:
+                torch.cuda.nvtx.range_pop()
             pr = ctx.profile_read() if profile else None
             ctx.profile(False)
             return sum(s.elapsed_time(e) for s, e in zip(starts, ends)), pr
 
         with Clocks(local) as clk:
-            ms, _ = timed(False)            # the reported step time: no stage events
+            ms, _ = timed(False, "sie_fp64")  # the reported step time: no stage events
             ms_prof, prof = timed(True)     # stage breakdown and roofline kernel times
         nested = op.stats()
         # end to end through host buffers (H2D of x and D2H of y inside the call)
@@ -214,7 +220,7 @@ def run_ours(args):
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        ms32, _ = timed(False)
+        ms32, _ = timed(False, "sie_mixed")
         _, prof32 = timed(True)
         op.set_solver(precision=sie.SIE_FP64)
         op.matvec(sie.SIE_OP_SYS, x, y64)

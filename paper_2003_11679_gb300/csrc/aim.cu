@@ -898,6 +898,8 @@ __global__ void k_interp(int nt, int S, int Mord, DevMesh M, const int32_t* __re
 
 // ------------------------------------------------------------------ near CSR product
 // y[m] += sum_e val[e] x[col[e]]; one warp per row
+// ACC: y += A x, else y = A x
+template <bool ACC>
 __global__ void __launch_bounds__(128) k_spmv(int nrow, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                               const double2* __restrict__ val, const double2* __restrict__ x,
                                               double2* __restrict__ y)
@@ -933,16 +935,19 @@ __global__ void __launch_bounds__(128) k_spmv(int nrow, const int64_t* __restric
         ai += __shfl_down_sync(0xffffffffu, ai, off);
     }
     if (lane == 0) {
-        y[r].x += ar;
-        y[r].y += ai;
+        if (ACC) {
+            y[r].x += ar;
+            y[r].y += ai;
+        } else {
+            y[r] = make_double2(ar, ai);
+        }
     }
 }
 
 sie_status csr_mv(cudaStream_t st, int nrow, const int64_t* rp, const int32_t* col, const double2* val,
                   const double2* x, double2* y)
 {
-    SIE_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double2) * nrow, st));
-    k_spmv<<<(nrow + 3) / 4, 128, 0, st>>>(nrow, rp, col, val, x, y);
+    k_spmv<false><<<(nrow + 3) / 4, 128, 0, st>>>(nrow, rp, col, val, x, y);
     SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
 }
@@ -966,8 +971,8 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
     sie_ctx* pc = op->mesh->ctx;
     cudaStream_t st = pc->stream;
     const DevMesh& M = op->mesh->d;
-    SIE_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double2) * M.ne, st));
     if (a.has_grid) {
+        SIE_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double2) * M.ne, st));
         const GridDesc& g = a.g;
         int S = (g.M + 1) * (g.M + 1) * (g.M + 1);
         int64_t Ng = (int64_t)g.N[0] * g.N[1] * g.N[2];
@@ -997,7 +1002,12 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
     }
     {
         Stage s_(pc, a.has_grid ? "spmv_aim" : "spmv_near_only");
-        k_spmv<<<(M.ne + 3) / 4, 128, 0, st>>>(M.ne, a.row_ptr, a.col, which_LK == 0 ? a.valL : a.valK, x, y);
+        // near-only operators have no grid term: the product overwrites y
+        const double2* v = which_LK == 0 ? a.valL : a.valK;
+        if (a.has_grid)
+            k_spmv<true><<<(M.ne + 3) / 4, 128, 0, st>>>(M.ne, a.row_ptr, a.col, v, x, y);
+        else
+            k_spmv<false><<<(M.ne + 3) / 4, 128, 0, st>>>(M.ne, a.row_ptr, a.col, v, x, y);
         SIE_CUDA_TRY(cudaGetLastError());
     }
     return SIE_OK;

@@ -191,6 +191,7 @@ struct KrylovWork {
     int64_t n = 0;
     int m = 0;
     double2 *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *r = nullptr, *part = nullptr;
+    double2* cgsp = nullptr;        // per-chunk partial sums of the fused Gram-Schmidt passes
     double2* Hd = nullptr;          // Hessenberg, rotations, g, y (device)
     double* sc = nullptr;           // |b|, beta, per-iteration relative residuals (device)
     double* resid_h = nullptr;      // pinned copies of the residuals

@@ -51,6 +51,8 @@ __global__ void k_jacobi(int64_t n, const double2* __restrict__ x, const double2
 // (chunk, vector) block, pass 2 sums the partials of each vector in a fixed
 // order (deterministic, and spread over the whole GPU for long vectors)
 constexpr int DOT_CHUNKS = 64;
+constexpr int CGS_CHUNKS = 128;  // row chunks of the fused Gram-Schmidt kernels
+constexpr int CGS_TILE = 32;     // columns per shared-memory tile there
 __global__ void __launch_bounds__(256) k_dots_part(int64_t n, const double2* __restrict__ V, int64_t ld,
                                                    const double2* __restrict__ w, double2* __restrict__ part)
 {
@@ -146,6 +148,7 @@ sie_status KrylovWork::alloc(cudaStream_t st, int64_t n_, int m_)
     SIE_CUDA_TRY(cudaMallocAsync((void**)&r, sizeof(double2) * n, st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&h, sizeof(double2) * 4 * (m + 2), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&part, sizeof(double2) * DOT_CHUNKS * (m + 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&cgsp, sizeof(double2) * CGS_CHUNKS * (2 * (m + 1) + 1), st));
     // Hessenberg (m+1) x m, rotations cs, sn, rhs g, solution y
     SIE_CUDA_TRY(cudaMallocAsync((void**)&Hd, sizeof(double2) * ((m + 1) * m + 2 * m + 2 * (m + 1)), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&sc, sizeof(double) * (8 + m + 1), st));
@@ -157,7 +160,7 @@ sie_status KrylovWork::alloc(cudaStream_t st, int64_t n_, int m_)
 
 void KrylovWork::release(cudaStream_t st)
 {
-    for (double2* p : {V, Z, w, h, r, part, Hd})
+    for (double2* p : {V, Z, w, h, r, part, cgsp, Hd})
         if (p) cudaFreeAsync(p, st);
     if (sc) cudaFreeAsync(sc, st);
     if (resid_h) {
@@ -166,7 +169,7 @@ void KrylovWork::release(cudaStream_t st)
     }
     for (auto& e : ev) cudaEventDestroy(e);
     ev.clear();
-    V = Z = w = h = r = part = Hd = nullptr;
+    V = Z = w = h = r = part = cgsp = Hd = nullptr;
     sc = nullptr;
     resid_h = nullptr;
     n = 0;
@@ -197,25 +200,10 @@ __global__ void k_gm_start(int64_t n, const double2* __restrict__ r, const doubl
     }
 }
 
-// column j of H from the two Gram-Schmidt passes; V_{j+1} = w / |w|
-__global__ void k_gm_next(int64_t n, int j, int m, const double2* __restrict__ h1, const double2* __restrict__ h2,
-                          const double2* __restrict__ wdot, const double2* __restrict__ w, double2* __restrict__ Vn,
-                          double2* __restrict__ H)
-{
-    double hn = sqrt(fmax(wdot[0].x, 0.0));
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        double s = hn > 0 ? 1.0 / hn : 0.0;
-        Vn[i] = make_double2(w[i].x * s, w[i].y * s);
-    }
-    if (i <= j) H[i * m + j] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
-    if (i == 0) H[(j + 1) * m + j] = make_double2(hn, 0);
-}
-
 // apply the previous rotations to column j, form rotation j (c real), update
-// g; relative residual |g[j+1]| / |b| to sc[3 + j]
-__global__ void k_gm_givens(int j, int m, double2* __restrict__ H, double2* __restrict__ cs, double2* __restrict__ sn,
-                            double2* __restrict__ g, double* __restrict__ sc)
+// g; relative residual |g[j+1]| / |b| to sc[3 + j]  (one thread)
+__device__ void gm_givens(int j, int m, double2* __restrict__ H, double2* __restrict__ cs, double2* __restrict__ sn,
+                          double2* __restrict__ g, double* __restrict__ sc)
 {
     for (int i = 0; i < j; i++) {
         double2 a = H[i * m + j], b = H[(i + 1) * m + j];
@@ -246,6 +234,134 @@ __global__ void k_gm_givens(int j, int m, double2* __restrict__ H, double2* __re
     g[j] = make_double2(c.x * gj.x, c.x * gj.y);
     g[j + 1] = make_double2(-t.x, -t.y);
     sc[3 + j] = (sc[0] > 0) ? hypot(g[j + 1].x, g[j + 1].y) / sc[0] : 0.0;
+}
+
+// Fused classical Gram-Schmidt, two passes.  The rows are split into
+// CGS_CHUNKS fixed chunks, one block each.  Every kernel first finishes, in a
+// fixed order, the reduction of the per-chunk partial sums the previous kernel
+// left, then updates its own rows and leaves the next partial sums: one
+// launch per pass instead of separate dot, reduction and update launches, and
+// the same rounding on every run.
+
+__device__ __forceinline__ void cgs_rows(int64_t n, int64_t& k0, int64_t& k1)
+{
+    const int64_t len = (n + CGS_CHUNKS - 1) / CGS_CHUNKS;
+    k0 = (int64_t)blockIdx.x * len;
+    k1 = min(n, k0 + len);
+}
+
+// P[c * ldp + i] = sum over rows k of chunk c of conj(V_i[k]) w[k], i < nv
+// (blockDim 256: 8 warps)
+__device__ void cgs_partials(int64_t k0, int64_t k1, int nv, const double2* __restrict__ V, int64_t ld,
+                             const double2* __restrict__ w, double2* __restrict__ P, int ldp)
+{
+    __shared__ double2 sm[8][CGS_TILE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i0 = 0; i0 < nv; i0 += CGS_TILE) {
+        const int ni = min(CGS_TILE, nv - i0);
+        for (int t = 0; t < ni; t++) {
+            const double2* v = V + (int64_t)(i0 + t) * ld;
+            double sr = 0, si = 0;
+            for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+                double2 a = v[k], b = w[k];
+                sr += a.x * b.x + a.y * b.y;
+                si += a.x * b.y - a.y * b.x;
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                sr += __shfl_down_sync(0xffffffffu, sr, off);
+                si += __shfl_down_sync(0xffffffffu, si, off);
+            }
+            if (lane == 0) sm[warp][t] = make_double2(sr, si);
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < ni) {
+            double2 s = sm[0][threadIdx.x];
+            for (int q = 1; q < 8; q++) {
+                s.x += sm[q][threadIdx.x].x;
+                s.y += sm[q][threadIdx.x].y;
+            }
+            P[(int64_t)blockIdx.x * ldp + i0 + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// pass 1: partial sums of V^H w
+__global__ void __launch_bounds__(256) k_cgs_part(int64_t n, int nv, const double2* __restrict__ V, int64_t ld,
+                                                  const double2* __restrict__ w, double2* __restrict__ P, int ldp)
+{
+    int64_t k0, k1;
+    cgs_rows(n, k0, k1);
+    cgs_partials(k0, k1, nv, V, ld, w, P, ldp);
+}
+
+// h = sum_c Pin[c][:] (block 0 stores it in hout); w -= V h on this chunk's
+// rows; then the partial sums of V^H w (last = 0) or of w^H w (last = 1)
+__global__ void __launch_bounds__(256) k_cgs_update(int64_t n, int nv, const double2* __restrict__ V, int64_t ld,
+                                                    const double2* __restrict__ Pin, int ldp,
+                                                    double2* __restrict__ hout, double2* __restrict__ w,
+                                                    double2* __restrict__ Pout, int last)
+{
+    __shared__ double2 h[CGS_TILE];
+    int64_t k0, k1;
+    cgs_rows(n, k0, k1);
+    for (int i0 = 0; i0 < nv; i0 += CGS_TILE) {
+        const int ni = min(CGS_TILE, nv - i0);
+        if ((int)threadIdx.x < ni) {
+            double2 s = make_double2(0, 0);
+            for (int c = 0; c < CGS_CHUNKS; c++) {
+                double2 p = Pin[(int64_t)c * ldp + i0 + threadIdx.x];
+                s.x += p.x;
+                s.y += p.y;
+            }
+            h[threadIdx.x] = s;
+            if (blockIdx.x == 0) hout[i0 + threadIdx.x] = s;
+        }
+        __syncthreads();
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+            double sr = 0, si = 0;
+            for (int t = 0; t < ni; t++) {
+                double2 a = V[(int64_t)(i0 + t) * ld + k], b = h[t];
+                sr += a.x * b.x - a.y * b.y;
+                si += a.x * b.y + a.y * b.x;
+            }
+            double2 o = w[k];
+            w[k] = make_double2(o.x - sr, o.y - si);
+        }
+        __syncthreads();
+    }
+    if (last)
+        cgs_partials(k0, k1, 1, w, 0, w, Pout, 1);
+    else
+        cgs_partials(k0, k1, nv, V, ld, w, Pout, ldp);
+}
+
+// |w| = sqrt(sum_c P[c]); V_{j+1} = w / |w| on this chunk's rows; block 0
+// writes column j of H (h1 + h2 and |w|) and applies the Givens step
+__global__ void __launch_bounds__(256) k_cgs_finish(int64_t n, int j, int m, const double2* __restrict__ h1,
+                                                    const double2* __restrict__ h2, const double2* __restrict__ P,
+                                                    const double2* __restrict__ w, double2* __restrict__ Vn,
+                                                    double2* __restrict__ H, double2* __restrict__ cs,
+                                                    double2* __restrict__ sn, double2* __restrict__ g,
+                                                    double* __restrict__ sc)
+{
+    __shared__ double hn_s;
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int c = 0; c < CGS_CHUNKS; c++) s += P[c].x;
+        hn_s = sqrt(fmax(s, 0.0));
+    }
+    __syncthreads();
+    const double hn = hn_s;
+    const double inv = hn > 0 ? 1.0 / hn : 0.0;
+    int64_t k0, k1;
+    cgs_rows(n, k0, k1);
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) Vn[k] = make_double2(w[k].x * inv, w[k].y * inv);
+    if (blockIdx.x != 0) return;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) H[i * m + j] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+    if (threadIdx.x == 0) H[(j + 1) * m + j] = make_double2(hn, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) gm_givens(j, m, H, cs, sn, g, sc);
 }
 
 // y = R^-1 g (upper triangular, size jend + 1)
@@ -287,21 +403,14 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
     double2* h1 = K.h;
     double2* h2 = K.h + (m + 2);
     double2* wd = K.h + 2 * (m + 2);
+    // x0 = 0, r0 = b.  No host round trip here: a zero b gives zero residuals
+    // (sc[3 + j] = 0), so the first convergence check stops with x = 0.
     SIE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
-    SIE_CUDA_TRY(cudaMemcpyAsync(K.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
-    SIE_TRY(dots(st, n, 1, K.r, n, K.r, K.part, wd));
-    k_gm_start<<<nb(n), 256, 0, st>>>(n, K.r, wd, K.V, g, m, K.sc, 1);
+    SIE_TRY(dots(st, n, 1, b, n, b, K.part, wd));
+    k_gm_start<<<nb(n), 256, 0, st>>>(n, b, wd, K.V, g, m, K.sc, 1);
     SIE_CUDA_TRY(cudaGetLastError());
-    SIE_CUDA_TRY(cudaMemcpyAsync(K.resid_h, K.sc, sizeof(double), cudaMemcpyDeviceToHost, st));
-    SIE_CUDA_TRY(cudaStreamSynchronize(st));
-    const double bnorm = K.resid_h[0];
     int it = 0;
     double rel = 1.0;
-    if (bnorm == 0.0) {
-        if (iters_out) *iters_out = 0;
-        if (relres_out) *relres_out = 0.0;
-        return SIE_OK;
-    }
     const int LAG = 1;
     while (true) {
         int j = 0;
@@ -311,14 +420,15 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
             double2* Zj = K.Z + (int64_t)j * n;
             SIE_TRY(Minv(Vj, Zj));
             SIE_TRY(A(Zj, K.w));
-            SIE_TRY(dots(st, n, j + 1, K.V, n, K.w, K.part, h1));
-            k_gemv<<<nb(n), 256, 0, st>>>(n, j + 1, K.V, n, h1, -1.0, K.w);
-            SIE_TRY(dots(st, n, j + 1, K.V, n, K.w, K.part, h2));
-            k_gemv<<<nb(n), 256, 0, st>>>(n, j + 1, K.V, n, h2, -1.0, K.w);
-            SIE_TRY(dots(st, n, 1, K.w, n, K.w, K.part, wd));
-            k_gm_next<<<nb(std::max<int64_t>(n, j + 1)), 256, 0, st>>>(n, j, m, h1, h2, wd, K.w,
-                                                                       K.V + (int64_t)(j + 1) * n, H);
-            k_gm_givens<<<1, 1, 0, st>>>(j, m, H, cs, sn, g, K.sc);
+            // CGS2: V^H w, w -= V h1, V^H w, w -= V h2, |w|, V_{j+1}, Givens
+            double2* P1 = K.cgsp;
+            double2* P2 = K.cgsp + (int64_t)CGS_CHUNKS * (m + 1);
+            double2* P3 = K.cgsp + (int64_t)2 * CGS_CHUNKS * (m + 1);
+            k_cgs_part<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K.V, n, K.w, P1, m + 1);
+            k_cgs_update<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K.V, n, P1, m + 1, h1, K.w, P2, 0);
+            k_cgs_update<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K.V, n, P2, m + 1, h2, K.w, P3, 1);
+            k_cgs_finish<<<CGS_CHUNKS, 256, 0, st>>>(n, j, m, h1, h2, P3, K.w, K.V + (int64_t)(j + 1) * n, H, cs,
+                                                      sn, g, K.sc);
             SIE_CUDA_TRY(cudaGetLastError());
             SIE_CUDA_TRY(cudaMemcpyAsync(K.resid_h + j, K.sc + 3 + j, sizeof(double), cudaMemcpyDeviceToHost, st));
             SIE_CUDA_TRY(cudaEventRecord(K.ev[j], st));
@@ -347,9 +457,9 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
         SIE_TRY(dots(st, n, 1, K.r, n, K.r, K.part, wd));
         k_gm_start<<<nb(n), 256, 0, st>>>(n, K.r, wd, K.V, g, m, K.sc, 0);
         SIE_CUDA_TRY(cudaGetLastError());
-        SIE_CUDA_TRY(cudaMemcpyAsync(K.resid_h, K.sc + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        SIE_CUDA_TRY(cudaMemcpyAsync(K.resid_h, K.sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         SIE_CUDA_TRY(cudaStreamSynchronize(st));
-        rel = K.resid_h[0] / bnorm;
+        rel = K.resid_h[0] > 0 ? K.resid_h[1] / K.resid_h[0] : 0.0;
         if (rel < tol) break;
     }
     if (iters_out) *iters_out = it;
