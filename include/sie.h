@@ -155,8 +155,9 @@ sie_status sie_op_destroy(sie_op* op);
 
 /* Replace the solver controls of a built operator: precision (grid path of
  * the system product: SIE_FP64 or SIE_MIXED = complex64 projection, FFT,
- * spectral multiply and interpolation with FP64 near-region products and
- * FP64 Krylov), tol_outer, tol_inner, maxit, restart, inner_maxit,
+ * spectral multiply and interpolation, exterior near-region products with
+ * complex64 copies of the FP64-integrated values (FP32 products, FP64 row
+ * sums), FP64 interior (lossy-medium) products and FP64 Krylov), tol_outer, tol_inner, maxit, restart, inner_maxit,
  * tol_constraint, constraint_maxit, constraint_restart, tol_constraint_inner are
  * taken from params;
  * grid and quadrature fields are ignored (they are fixed at build time). */

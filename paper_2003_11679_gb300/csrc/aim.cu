@@ -13,6 +13,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "spmv.cuh"
 
 namespace sie {
 
@@ -110,6 +111,15 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
+}
+
+// complex64 copy of a complex128 array (allocated here)
+static sie_status to_c64(cudaStream_t st, const double2* a, int64_t n, float2** out)
+{
+    SIE_CUDA_TRY(cudaMallocAsync((void**)out, sizeof(float2) * std::max<int64_t>(n, 1), st));
+    if (n > 0) k_to_f32<<<(unsigned)((2 * n + 255) / 256), 256, 0, st>>>((const double*)a, (float*)*out, 2 * n);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
 }
 
 sie_status aim_weights(sie_op* op)
@@ -898,57 +908,11 @@ __global__ void k_interp(int nt, int S, int Mord, DevMesh M, const int32_t* __re
 
 // ------------------------------------------------------------------ near CSR product
 // y[m] += sum_e val[e] x[col[e]]; one warp per row
-// ACC: y += A x, else y = A x
-template <bool ACC>
-__global__ void __launch_bounds__(128) k_spmv(int nrow, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                              const double2* __restrict__ val, const double2* __restrict__ x,
-                                              double2* __restrict__ y)
-{
-    int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    int lane = threadIdx.x & 31;
-    if (r >= nrow) return;
-    double ar = 0, ai = 0;
-    const int64_t e1 = rp[r + 1];
-    int64_t e = rp[r] + lane;
-    for (; e + 96 < e1; e += 128) {  // 4 independent loads per lane in flight
-        int c[4];
-        double2 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            c[u] = __ldg(col + e + 32 * u);
-            v[u] = __ldg(val + e + 32 * u);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            double2 xv = __ldg(x + c[u]);
-            ar += v[u].x * xv.x - v[u].y * xv.y;
-            ai += v[u].x * xv.y + v[u].y * xv.x;
-        }
-    }
-    for (; e < e1; e += 32) {
-        double2 v = val[e], xv = x[col[e]];
-        ar += v.x * xv.x - v.y * xv.y;
-        ai += v.x * xv.y + v.y * xv.x;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        ar += __shfl_down_sync(0xffffffffu, ar, off);
-        ai += __shfl_down_sync(0xffffffffu, ai, off);
-    }
-    if (lane == 0) {
-        if (ACC) {
-            y[r].x += ar;
-            y[r].y += ai;
-        } else {
-            y[r] = make_double2(ar, ai);
-        }
-    }
-}
 
-sie_status csr_mv(cudaStream_t st, int nrow, const int64_t* rp, const int32_t* col, const double2* val,
-                  const double2* x, double2* y)
+sie_status csr_mv(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp, const int32_t* col,
+                  const double2* val, const double2* x, double2* y)
 {
-    k_spmv<false><<<(nrow + 3) / 4, 128, 0, st>>>(nrow, rp, col, val, x, y);
-    SIE_CUDA_TRY(cudaGetLastError());
+    SIE_CUDA_TRY(csr_launch(st, nrow, nnz, rp, col, val, x, make_double2(1.0, 0.0), false, y));
     return SIE_OK;
 }
 
@@ -1004,10 +968,7 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
         Stage s_(pc, a.has_grid ? "spmv_aim" : "spmv_near_only");
         // near-only operators have no grid term: the product overwrites y
         const double2* v = which_LK == 0 ? a.valL : a.valK;
-        if (a.has_grid)
-            k_spmv<true><<<(M.ne + 3) / 4, 128, 0, st>>>(M.ne, a.row_ptr, a.col, v, x, y);
-        else
-            k_spmv<false><<<(M.ne + 3) / 4, 128, 0, st>>>(M.ne, a.row_ptr, a.col, v, x, y);
+        SIE_CUDA_TRY(csr_launch(st, M.ne, a.nnz, a.row_ptr, a.col, v, x, make_double2(1.0, 0.0), a.has_grid, y));
         SIE_CUDA_TRY(cudaGetLastError());
     }
     return SIE_OK;
@@ -1016,10 +977,11 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
 static void free_aim(AimOp& a)
 {
     void* ptrs[] = {a.spec, a.spec32, a.pairs, a.row_ptr, a.col, a.valL, a.valK, a.valLA, a.dLA, a.dL,
-                    a.tri_row_ptr, a.tri_col, a.valLphi, a.valLphiNR, a.valM};
+                    a.tri_row_ptr, a.tri_col, a.valLphi, a.valLphiNR, a.valM, a.valLA32, a.valK32, a.valLphi32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     a.valLA = a.dLA = a.dL = a.valLphi = a.valLphiNR = a.valM = nullptr;
+    a.valLA32 = a.valK32 = a.valLphi32 = nullptr;
     a.tri_row_ptr = nullptr;
     a.tri_col = nullptr;
     a.spec = nullptr;
@@ -1113,6 +1075,13 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
     auto t2 = now();
     op->build_ms[3] = ms(t1, t2);
     if ((s = near_build(op, op->ext, q)) != SIE_OK) return fail(s);
+    {
+        AimOp& X = op->ext;
+        const int64_t ntri = X.tri_row_ptr_h.empty() ? 0 : X.tri_row_ptr_h.back();
+        if ((s = to_c64(st, X.valLA, X.nnz, &X.valLA32)) != SIE_OK || (s = to_c64(st, X.valK, X.nnz, &X.valK32)) != SIE_OK ||
+            (s = to_c64(st, X.valLphi, ntri, &X.valLphi32)) != SIE_OK)
+            return fail(s);
+    }
     auto t3 = now();
     op->build_ms[1] = ms(t2, t3);
     // interior operator (Sec. III-C): near-only when every pair inside the

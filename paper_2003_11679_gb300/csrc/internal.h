@@ -135,6 +135,10 @@ struct AimOp {
     double2* valLphi = nullptr;
     double2* valLphiNR = nullptr;   // exact near Lphi (constraint preconditioner)
     double2* valM = nullptr;        // sparse approximate inverse of valL (near-only interiors)
+    // complex64 copies of the exterior near values for the mixed-precision product
+    float2* valLA32 = nullptr;
+    float2* valK32 = nullptr;
+    float2* valLphi32 = nullptr;
 };
 
 struct Workspace {
@@ -215,6 +219,7 @@ struct sie_op {
     double build_ms[4] = {0, 0, 0, 0};  // weights+spectra, exterior near, interior near, host lists
     // system operator (Eq. sys)
     int64_t* ix_row_ptr = nullptr;  // Ix as edge CSR (real values stored as double2)
+    int64_t ix_nnz = 0;
     int32_t* ix_col = nullptr;
     double2* ix_val = nullptr;
     double* elen = nullptr;         // edge lengths
@@ -242,8 +247,8 @@ sie_status sys_matvec(sie_op* op, int which, const double2* x, double2* y);
 sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres);
 sie_status sys_rhs(sie_op* op, const double* khat, const double* epol, double2* b);
 // y = A x for an edge CSR matrix (overwrites y)
-sie_status csr_mv(cudaStream_t st, int nrow, const int64_t* rp, const int32_t* col, const double2* val,
-                  const double2* x, double2* y);
+sie_status csr_mv(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp, const int32_t* col,
+                  const double2* val, const double2* x, double2* y);
 sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, double* rcs);
 bool sys_z_workspace_ready(const sie_op* op);
 sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int ndir, double2* sums);

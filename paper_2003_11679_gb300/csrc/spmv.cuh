@@ -1,0 +1,107 @@
+// CSR sparse products (complex128) for the near-region matrices.
+//
+// A group of G lanes (G = 4, 8 or 32) works on one row; each lane keeps four
+// (column, value) loads and then four gathers of x in flight before using
+// them, so that short rows (the near-only interior operators hold ~30 entries
+// per row) are not one long dependent load chain per warp.  The group sums by
+// a fixed xor-shuffle tree: the result is the same on every run.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sie {
+
+// VT = double2: FP64 throughout.  VT = float2 (complex64 values of the mixed
+// precision path): FP32 products and per-lane sums, the group sum in FP64.
+template <int G, class VT>
+__device__ __forceinline__ double2 csr_row_dot(int64_t e0, int64_t e1, const int32_t* __restrict__ col,
+                                               const VT* __restrict__ val, const double2* __restrict__ x, int l)
+{
+    using R = decltype(VT{}.x);
+    R ar = 0, ai = 0;
+    int64_t e = e0 + l;
+    for (; e + 3 * G < e1; e += 4 * G) {
+        int c[4];
+        VT v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            c[u] = __ldg(col + e + u * G);
+            v[u] = __ldg(val + e + u * G);
+        }
+        double2 xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) xv[u] = __ldg(x + c[u]);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const R xr = (R)xv[u].x, xi = (R)xv[u].y;
+            ar += v[u].x * xr - v[u].y * xi;
+            ai += v[u].x * xi + v[u].y * xr;
+        }
+    }
+    for (; e < e1; e += G) {
+        VT v = __ldg(val + e);
+        double2 xd = __ldg(x + __ldg(col + e));
+        const R xr = (R)xd.x, xi = (R)xd.y;
+        ar += v.x * xr - v.y * xi;
+        ai += v.x * xi + v.y * xr;
+    }
+    double sr = ar, si = ai;
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, off);
+        si += __shfl_xor_sync(0xffffffffu, si, off);
+    }
+    return make_double2(sr, si);
+}
+
+// y = alpha A x (ACC = false) or y += alpha A x (ACC = true); blockDim 256
+template <int G, bool ACC, class VT>
+__global__ void __launch_bounds__(256) k_csr(int nrow, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                             const VT* __restrict__ val, const double2* __restrict__ x,
+                                             double2 alpha, double2* __restrict__ y)
+{
+    const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G);
+    const int l = threadIdx.x % G;
+    const bool ok = r < nrow;
+    // rows past the end still take part in the shuffles, with an empty range
+    const int64_t e0 = ok ? __ldg(rp + r) : 0, e1 = ok ? __ldg(rp + r + 1) : 0;
+    const double2 s = csr_row_dot<G, VT>(e0, e1, col, val, x, l);
+    if (ok && l == 0) {
+        double2 t = make_double2(alpha.x * s.x - alpha.y * s.y, alpha.x * s.y + alpha.y * s.x);
+        if (ACC) {
+            double2 o = y[r];
+            t.x += o.x;
+            t.y += o.y;
+        }
+        y[r] = t;
+    }
+}
+
+// lanes per row from the mean row length
+inline int csr_group(int64_t nrow, int64_t nnz)
+{
+    const int64_t avg = nrow > 0 ? nnz / nrow : 0;
+    return avg <= 12 ? 4 : (avg <= 48 ? 8 : 32);
+}
+
+template <class VT>
+inline cudaError_t csr_launch(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp, const int32_t* col,
+                              const VT* val, const double2* x, double2 alpha, bool acc, double2* y)
+{
+    if (nrow <= 0) return cudaSuccess;
+    const int G = csr_group(nrow, nnz);
+    const unsigned blocks = (unsigned)(((int64_t)nrow * G + 255) / 256);
+    if (G == 4) {
+        if (acc) k_csr<4, true, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+        else k_csr<4, false, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+    } else if (G == 8) {
+        if (acc) k_csr<8, true, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+        else k_csr<8, false, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+    } else {
+        if (acc) k_csr<32, true, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+        else k_csr<32, false, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sie

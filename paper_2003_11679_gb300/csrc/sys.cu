@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "spmv.cuh"
 
 namespace sie {
 
@@ -307,15 +308,23 @@ __global__ void __launch_bounds__(256) k_cgs_update(int64_t n, int nv, const dou
     cgs_rows(n, k0, k1);
     for (int i0 = 0; i0 < nv; i0 += CGS_TILE) {
         const int ni = min(CGS_TILE, nv - i0);
-        if ((int)threadIdx.x < ni) {
-            double2 s = make_double2(0, 0);
-            for (int c = 0; c < CGS_CHUNKS; c++) {
-                double2 p = Pin[(int64_t)c * ldp + i0 + threadIdx.x];
-                s.x += p.x;
-                s.y += p.y;
+        // one warp per column: lanes take every 32nd chunk, then a fixed xor tree
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int t = warp; t < ni; t += 8) {
+            double sr = 0, si = 0;
+            for (int c = lane; c < CGS_CHUNKS; c += 32) {
+                double2 p = Pin[(int64_t)c * ldp + i0 + t];
+                sr += p.x;
+                si += p.y;
             }
-            h[threadIdx.x] = s;
-            if (blockIdx.x == 0) hout[i0 + threadIdx.x] = s;
+            for (int off = 16; off > 0; off >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, off);
+                si += __shfl_xor_sync(0xffffffffu, si, off);
+            }
+            if (lane == 0) {
+                h[t] = make_double2(sr, si);
+                if (blockIdx.x == 0) hout[i0 + t] = h[t];
+            }
         }
         __syncthreads();
         for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
@@ -346,10 +355,11 @@ __global__ void __launch_bounds__(256) k_cgs_finish(int64_t n, int j, int m, con
                                                     double* __restrict__ sc)
 {
     __shared__ double hn_s;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         double s = 0;
-        for (int c = 0; c < CGS_CHUNKS; c++) s += P[c].x;
-        hn_s = sqrt(fmax(s, 0.0));
+        for (int c = threadIdx.x; c < CGS_CHUNKS; c += 32) s += P[c].x;
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) hn_s = sqrt(fmax(s, 0.0));
     }
     __syncthreads();
     const double hn = hn_s;
@@ -642,44 +652,60 @@ __global__ void k_specmul_sys(const double2* __restrict__ spec, double2* __restr
     buf[3 * nn + i] = mul(G, buf[6 * nn + i]);
 }
 
-// y[r] += alpha * sum_e val[e] x[col[e]]
-__global__ void __launch_bounds__(128) k_spmv_a(int nrow, const int64_t* __restrict__ rp,
-                                                const int32_t* __restrict__ col, const double2* __restrict__ val,
-                                                const double2* __restrict__ x, double2 alpha, double2* __restrict__ y)
+// k_spmv2 with complex64 values (SIE_MIXED): FP32 products and per-lane sums,
+// the lane sums combined in FP64
+__global__ void __launch_bounds__(128) k_spmv2_32(int nrow, const int64_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ col, const float2* __restrict__ v1,
+                                                  const double2* __restrict__ x1, double2 a1,
+                                                  const float2* __restrict__ v2, const double2* __restrict__ x2,
+                                                  double2 a2, double2* __restrict__ y)
 {
     int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (r >= nrow) return;
-    double ar = 0, ai = 0;
-    const int64_t e1 = rp[r + 1];
-    int64_t e = rp[r] + lane;
+    float s1r = 0, s1i = 0, s2r = 0, s2i = 0;
+    const int64_t e0 = rp[r], e1 = rp[r + 1];
+    int64_t e = e0 + lane;
     for (; e + 96 < e1; e += 128) {
         int c[4];
-        double2 v[4];
+        float2 p[4], q[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) c[u] = __ldg(col + e + 32 * u);
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            c[u] = __ldg(col + e + 32 * u);
-            v[u] = __ldg(val + e + 32 * u);
+            p[u] = __ldg(v1 + e + 32 * u);
+            q[u] = __ldg(v2 + e + 32 * u);
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            double2 xv = __ldg(x + c[u]);
-            ar += v[u].x * xv.x - v[u].y * xv.y;
-            ai += v[u].x * xv.y + v[u].y * xv.x;
+            double2 xa = __ldg(x1 + c[u]), xb = __ldg(x2 + c[u]);
+            float ar = (float)xa.x, ai = (float)xa.y, br = (float)xb.x, bi = (float)xb.y;
+            s1r += p[u].x * ar - p[u].y * ai;
+            s1i += p[u].x * ai + p[u].y * ar;
+            s2r += q[u].x * br - q[u].y * bi;
+            s2i += q[u].x * bi + q[u].y * br;
         }
     }
     for (; e < e1; e += 32) {
-        double2 v = val[e], xv = x[col[e]];
-        ar += v.x * xv.x - v.y * xv.y;
-        ai += v.x * xv.y + v.y * xv.x;
+        int c = col[e];
+        float2 p = v1[e], q = v2[e];
+        double2 xa = x1[c], xb = x2[c];
+        float ar = (float)xa.x, ai = (float)xa.y, br = (float)xb.x, bi = (float)xb.y;
+        s1r += p.x * ar - p.y * ai;
+        s1i += p.x * ai + p.y * ar;
+        s2r += q.x * br - q.y * bi;
+        s2i += q.x * bi + q.y * br;
     }
+    double t1r = s1r, t1i = s1i, t2r = s2r, t2i = s2i;
     for (int off = 16; off > 0; off >>= 1) {
-        ar += __shfl_down_sync(0xffffffffu, ar, off);
-        ai += __shfl_down_sync(0xffffffffu, ai, off);
+        t1r += __shfl_down_sync(0xffffffffu, t1r, off);
+        t1i += __shfl_down_sync(0xffffffffu, t1i, off);
+        t2r += __shfl_down_sync(0xffffffffu, t2r, off);
+        t2i += __shfl_down_sync(0xffffffffu, t2i, off);
     }
     if (lane == 0) {
-        y[r].x += alpha.x * ar - alpha.y * ai;
-        y[r].y += alpha.x * ai + alpha.y * ar;
+        y[r].x += a1.x * t1r - a1.y * t1i + a2.x * t2r - a2.y * t2i;
+        y[r].y += a1.x * t1i + a1.y * t1r + a2.x * t2i + a2.y * t2r;
     }
 }
 
@@ -736,13 +762,15 @@ __global__ void __launch_bounds__(128) k_spmv2(int nrow, const int64_t* __restri
     }
 }
 
-static sie_status spmv(cudaStream_t st, int nrow, const int64_t* rp, const int32_t* col, const double2* val,
-                       const double2* x, cplx alpha, double2* y)
+// y += alpha A x (acc) or y = alpha A x for a CSR matrix with nnz entries
+static sie_status spmv(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp, const int32_t* col,
+                       const double2* val, const double2* x, cplx alpha, double2* y, bool acc = true)
 {
-    k_spmv_a<<<(nrow + 3) / 4, 128, 0, st>>>(nrow, rp, col, val, x, make_double2(alpha.real(), alpha.imag()), y);
-    SIE_CUDA_TRY(cudaGetLastError());
+    SIE_CUDA_TRY(csr_launch(st, nrow, nnz, rp, col, val, x, make_double2(alpha.real(), alpha.imag()), acc, y));
     return SIE_OK;
 }
+
+static int64_t tri_nnz(const AimOp& a) { return a.tri_row_ptr_h.empty() ? 0 : a.tri_row_ptr_h.back(); }
 
 // sigma_t = -A_t c0rho_t
 __global__ void k_sigma(int nt, const double* __restrict__ area, const double2* __restrict__ rho,
@@ -930,7 +958,7 @@ static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_i
     const int64_t ne = op->mesh->h.ne;
     double2* a = op->sys_tmp;  // ne
     SIE_TRY(aim_apply(op, op->inn, 1, H, a));
-    SIE_TRY(spmv(st, (int)ne, op->ix_row_ptr, op->ix_col, op->ix_val, H, cplx(-0.5, 0), a));
+    SIE_TRY(spmv(st, (int)ne, op->ix_nnz, op->ix_row_ptr, op->ix_col, op->ix_val, H, cplx(-0.5, 0), a));
     AimOp& I = op->inn;
     Apply A = [&](const double2* x, double2* y) { return aim_apply(op, I, 0, x, y); };
     cplx ki(I.kr, I.ki);
@@ -947,7 +975,7 @@ static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_i
     } else {
         Minv = [&](const double2* x, double2* y) {
             Stage s_(c, "spai_apply");
-            return csr_mv(st, (int)ne, I.row_ptr, I.col, I.valM, x, y);
+            return csr_mv(st, (int)ne, I.nnz, I.row_ptr, I.col, I.valM, x, y);
         };
     }
     int it = 0;
@@ -1033,16 +1061,26 @@ static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
     }
     {
         Stage s_(c, "spmv_sys");
-        k_spmv2<<<(unsigned)((ne + 3) / 4), 128, 0, st>>>((int)ne, X.row_ptr, X.col, X.valLA, H,
-                                                           make_double2(0.0, op->k0), X.valK, E,
-                                                           make_double2(-1.0, 0.0), y1);
+        const bool c64 = op->p.precision == SIE_MIXED && X.valLA32;
+        if (c64)
+            k_spmv2_32<<<(unsigned)((ne + 3) / 4), 128, 0, st>>>((int)ne, X.row_ptr, X.col, X.valLA32, H,
+                                                                  make_double2(0.0, op->k0), X.valK32, E,
+                                                                  make_double2(-1.0, 0.0), y1);
+        else
+            k_spmv2<<<(unsigned)((ne + 3) / 4), 128, 0, st>>>((int)ne, X.row_ptr, X.col, X.valLA, H,
+                                                               make_double2(0.0, op->k0), X.valK, E,
+                                                               make_double2(-1.0, 0.0), y1);
         SIE_CUDA_TRY(cudaGetLastError());
-        SIE_TRY(spmv(st, (int)ne, op->ix_row_ptr, op->ix_col, op->ix_val, E, cplx(-0.5, 0.0), y1));
+        SIE_TRY(spmv(st, (int)ne, op->ix_nnz, op->ix_row_ptr, op->ix_col, op->ix_val, E, cplx(-0.5, 0.0), y1));
         double2* sig = op->sys_tmp;
         double2* phi = op->sys_tmp + nt;
         k_sigma<<<nb(nt), 256, 0, st>>>((int)nt, M.area, rho, sig);
-        SIE_CUDA_TRY(cudaMemsetAsync(phi, 0, sizeof(double2) * nt, st));
-        SIE_TRY(spmv(st, (int)nt, X.tri_row_ptr, X.tri_col, X.valLphi, sig, cplx(1.0, 0.0), phi));
+        if (c64)
+            SIE_CUDA_TRY(csr_launch(st, (int)nt, tri_nnz(X), X.tri_row_ptr, X.tri_col, X.valLphi32, sig,
+                                    make_double2(1.0, 0.0), false, phi));
+        else
+            SIE_TRY(spmv(st, (int)nt, tri_nnz(X), X.tri_row_ptr, X.tri_col, X.valLphi, sig, cplx(1.0, 0.0), phi,
+                         false));
         k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, phi, y1);
         k_row2<<<nb(nt), 256, 0, st>>>((int)nt, M, H, rho, op->k0, y2);
         SIE_CUDA_TRY(cudaGetLastError());
@@ -1075,8 +1113,7 @@ static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork&
     SIE_CUDA_TRY(cudaGetLastError());
     Apply S = [&](const double2* x, double2* out) {
         // out = x - kappa D Dg^-1 D^T Lphi x
-        SIE_CUDA_TRY(cudaMemsetAsync(ph, 0, sizeof(double2) * nt, st));
-        SIE_TRY(spmv(st, (int)nt, a.tri_row_ptr, a.tri_col, a.valLphiNR, x, 1.0, ph));
+        SIE_TRY(spmv(st, (int)nt, tri_nnz(a), a.tri_row_ptr, a.tri_col, a.valLphiNR, x, 1.0, ph, false));
         SIE_CUDA_TRY(cudaMemsetAsync(te, 0, sizeof(double2) * ne, st));
         k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, ph, te);
         k_jacobi<<<nb(ne), 256, 0, st>>>(ne, te, a.dLA, make_double2(1.0, 0.0), te);
@@ -1099,8 +1136,7 @@ static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork&
     op->stats[5] = std::max(op->stats[5], rr);
     if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
     // y = Dg^-1 (v + kappa D^T Lphi q)
-    SIE_CUDA_TRY(cudaMemsetAsync(ph, 0, sizeof(double2) * nt, st));
-    SIE_TRY(spmv(st, (int)nt, a.tri_row_ptr, a.tri_col, a.valLphiNR, q, 1.0, ph));
+    SIE_TRY(spmv(st, (int)nt, tri_nnz(a), a.tri_row_ptr, a.tri_col, a.valLphiNR, q, 1.0, ph, false));
     SIE_CUDA_TRY(cudaMemsetAsync(te, 0, sizeof(double2) * ne, st));
     k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, ph, te);
     SIE_CUDA_TRY(cudaGetLastError());
@@ -1127,8 +1163,7 @@ static sie_status precond_sys(sie_op* op, const double2* x, double2* y)
     double2* ph = op->pc_t + nt;      // nt
     // v1' = v1 - (j k0)^-1 D^T Lphi B v2,  B v2 = -A v2
     k_sigma<<<nb(nt), 256, 0, st>>>((int)nt, M.area, x + ne, sig);
-    SIE_CUDA_TRY(cudaMemsetAsync(ph, 0, sizeof(double2) * nt, st));
-    SIE_TRY(spmv(st, (int)nt, X.tri_row_ptr, X.tri_col, X.valLphiNR, sig, 1.0, ph));
+    SIE_TRY(spmv(st, (int)nt, tri_nnz(X), X.tri_row_ptr, X.tri_col, X.valLphiNR, sig, 1.0, ph, false));
     SIE_CUDA_TRY(cudaMemsetAsync(v1p, 0, sizeof(double2) * ne, st));
     k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, ph, v1p);
     SIE_CUDA_TRY(cudaGetLastError());
@@ -1183,6 +1218,7 @@ sie_status sys_prepare(sie_op* op)
         }
         rp[m + 1] = (int64_t)col.size();
     }
+    op->ix_nnz = (int64_t)col.size();
     SIE_CUDA_TRY(cudaMallocAsync((void**)&op->ix_row_ptr, sizeof(int64_t) * rp.size(), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&op->ix_col, sizeof(int32_t) * col.size(), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&op->ix_val, sizeof(double2) * val.size(), st));

@@ -104,9 +104,10 @@ def test_solve_rcs_matches_mie(lib, case, request):
 
 @pytest.mark.parametrize("case", ["diel", "lossy"])
 def test_mixed_precision_system_product(lib, case, request):
-    """Complex64 grid path (SIE_MIXED): the system product stays within 1e-5 of
-    the FP64 product (FP32 rounding of the grid part only; near-region
-    products and all vectors stay FP64)."""
+    """Complex64 path (SIE_MIXED): the system product stays within 1e-5 of the
+    FP64 product (FP32 rounding of the grid part and of the exterior
+    near-region values and products; the interior operators, the row sums and
+    all vectors stay FP64)."""
     c = request.getfixturevalue(case)
     x = np.concatenate([cn_vector(c.ne, 81), cn_vector(c.nt, 82)])
     y64 = c.op.matvec(lib.SIE_OP_SYS, x)
