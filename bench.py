@@ -206,6 +206,7 @@ def run_ours(args):
             ms, _ = timed(False, "sie_fp64")  # the reported step time: no stage events
             ms_prof, prof = timed(True)     # stage breakdown and roofline kernel times
         nested = op.stats()
+        graph_state = int(op.info()[16])  # +1: FP64 system-product graph captured (used by the timed loop)
         # end to end through host buffers (H2D of x and D2H of y inside the call)
         xh = cn_vector(n, 1 + rank)
         yh = np.zeros_like(xh)
@@ -276,6 +277,9 @@ def run_ours(args):
         "gpu_launches": launches,
         "ms_per_step_with_stage_events": ms_prof / args.steps,
         "nested_solves": nested,
+        "system_graph": {"fp64": bool(graph_state & 1), "capture_failed": bool(graph_state & 4),
+                         "note": "timed loop replays one CUDA graph per product (nested solve as a device-ended "
+                                 "loop); the stage breakdown comes from the stream path with per-stage events"},
         "solves": solves,
         "mixed_precision": mixed_line(ne, args, ms32, prof32, mixed_err, info, peaks, kind),
         "stages_ms": {k: round(v[0], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},

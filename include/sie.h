@@ -157,10 +157,10 @@ sie_status sie_op_destroy(sie_op* op);
  * the system product: SIE_FP64 or SIE_MIXED = complex64 projection, FFT,
  * spectral multiply and interpolation, exterior near-region products with
  * complex64 copies of the FP64-integrated values (FP32 products, FP64 row
- * sums), FP64 interior (lossy-medium) products and FP64 Krylov), tol_outer, tol_inner, maxit, restart, inner_maxit,
- * tol_constraint, constraint_maxit, constraint_restart, tol_constraint_inner are
- * taken from params;
- * grid and quadrature fields are ignored (they are fixed at build time). */
+ * sums), FP64 interior (lossy-medium) products and FP64 Krylov), tol_outer,
+ * tol_inner, maxit, restart, inner_maxit, tol_constraint, constraint_maxit,
+ * constraint_restart and tol_constraint_inner are taken from params; grid and
+ * quadrature fields are ignored (they are fixed at build time). */
 sie_status sie_op_set_solver(sie_op* op, const sie_params* params);
 
 /* Statistics of the last sie_solve on this operator (6 doubles): outer
@@ -174,14 +174,23 @@ sie_status sie_op_stats(const sie_op* op, double out[6]);
  * near matrix; [9] interior mode (0 = AIM, 1 = near only); [10] interior near
  * pairs; [11] grid origin x (origin y, z: see sie_op_grid); build wall times
  * in ms: [12] weights and spectra, [13] exterior near region, [14] interior
- * near region, [15] host-side pair lists. */
-sie_status sie_op_info(const sie_op* op, double info[16]);
+ * near region, [15] host-side pair lists; [16] system-product CUDA graph
+ * (near-region-only interiors): +1 captured for SIE_FP64, +2 for SIE_MIXED,
+ * +4 capture failed (the stream path is used); [17..19] reserved (0). */
+sie_status sie_op_info(const sie_op* op, double info[20]);
 /* grid origin (3) and spacing of the exterior grid */
 sie_status sie_op_grid(const sie_op* op, double origin[3], double* h, int64_t N[3]);
 
 /* y = A x for nrhs right-hand sides, A selected by `which` (SIE_OP_*).
- * x, y: complex128, length N_e (SYS: N_e as well: the AEFIE charge rows are
- * eliminated, see sie_solve).  flags: SIE_DEVICE_PTRS or 0. */
+ * x, y: complex128, length N_e (L0, K0, LI, KI, ZI) or N_e + N_t (SYS, the
+ * AEFIE unknowns [H; c0 rho] of Eq. sys).  flags: SIE_DEVICE_PTRS or 0.
+ * When the interior operator is near-region only and profiling is off, the
+ * SYS product (nested solve of Eq. nest2 included) is captured on first use
+ * into a CUDA graph, one per precision, and replayed; the nested iterations
+ * are then a loop the device ends itself (at most min(restart, 60) and
+ * inner_maxit iterations, no restart).  The environment variable SIE_GRAPH=0
+ * selects the stream path.  The graph is dropped when tol_inner, inner_maxit
+ * or restart change (sie_op_set_solver). */
 sie_status sie_matvec(sie_op* op, int which, const double* x, double* y, int nrhs, int flags);
 
 /* Export the precorrected near-region matrix of an operator

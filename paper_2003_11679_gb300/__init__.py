@@ -182,7 +182,7 @@ class Operator:
         _check(lib().sie_op_build(mesh.h, freq, eps_r, mu_r, sigma, ctypes.byref(p), ctypes.byref(self.h)))
 
     def info(self):
-        a = np.zeros(16)
+        a = np.zeros(20)
         _check(lib().sie_op_info(self.h, a.ctypes.data))
         return a
 

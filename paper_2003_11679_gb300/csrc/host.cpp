@@ -534,7 +534,7 @@ sie_status sie_mesh_counts(const sie_mesh* m, int64_t out[3])
     return SIE_OK;
 }
 
-sie_status sie_op_info(const sie_op* op, double info[16])
+sie_status sie_op_info(const sie_op* op, double info[20])
 {
     if (!op || !info) return SIE_ERR_ARG;
     const GridDesc& g = op->ext.g;
@@ -549,6 +549,8 @@ sie_status sie_op_info(const sie_op* op, double info[16])
     info[10] = (double)op->inn.npairs;
     info[11] = g.o[0];
     for (int i = 0; i < 4; i++) info[12 + i] = op->build_ms[i];
+    info[16] = (op->gexec[0] ? 1.0 : 0.0) + (op->gexec[1] ? 2.0 : 0.0) + (op->gfailed ? 4.0 : 0.0);
+    for (int i = 17; i < 20; i++) info[i] = 0.0;
     return SIE_OK;
 }
 
@@ -559,6 +561,9 @@ sie_status sie_op_set_solver(sie_op* op, const sie_params* p)
         set_error("sie_op_set_solver: invalid argument");
         return SIE_ERR_ARG;
     }
+    // the captured system-product graph bakes in the nested-solve settings
+    if (p->tol_inner != op->p.tol_inner || p->inner_maxit != op->p.inner_maxit || p->restart != op->p.restart)
+        sie::sys_graph_reset(op);
     op->p.tol_outer = p->tol_outer;
     op->p.tol_inner = p->tol_inner;
     op->p.maxit = p->maxit;
@@ -575,6 +580,7 @@ sie_status sie_op_set_solver(sie_op* op, const sie_params* p)
 sie_status sie_op_stats(const sie_op* op, double out[6])
 {
     if (!op || !out) return SIE_ERR_ARG;
+    sie::sys_stats_fold(const_cast<sie_op*>(op));  // nested-solve counts of graph runs
     for (int i = 0; i < 6; i++) out[i] = op->stats[i];
     return SIE_OK;
 }

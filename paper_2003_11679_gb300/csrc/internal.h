@@ -196,6 +196,8 @@ struct KrylovWork {
     int m = 0;
     double2 *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *r = nullptr, *part = nullptr;
     double2* cgsp = nullptr;        // per-chunk partial sums of the fused Gram-Schmidt passes
+    double2* dv = nullptr;          // device-controlled cycle: v_j and z_j (2 n)
+    int* dj = nullptr;              // device-controlled cycle: iteration index, iterations done
     double2* Hd = nullptr;          // Hessenberg, rotations, g, y (device)
     double* sc = nullptr;           // |b|, beta, per-iteration relative residuals (device)
     double* resid_h = nullptr;      // pinned copies of the residuals
@@ -230,6 +232,14 @@ struct sie_op {
     double2 *cs_e = nullptr, *cs_t = nullptr, *pc_e = nullptr, *pc_t = nullptr;  // preconditioner scratch
     // last solve: outer iters, relres; max nested iters, relres; max constraint iters, relres
     double stats[6] = {0, 0, 0, 0, 0, 0};
+    // CUDA graph of the system product (near-only interior, profiling off): the
+    // nested solve is a device-controlled while loop inside the graph
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // one per precision (SIE_FP64, SIE_MIXED)
+    bool gfailed = false;           // capture or instantiation failed: stream path only
+    bool capturing = false;         // apply_Z emits the device-controlled nested solve
+    cudaStream_t gs[2] = {nullptr, nullptr};  // capture streams: graph, while-loop body
+    double2* g_io = nullptr;        // graph input x and output y, 2 (ne + nt)
+    double* gstat = nullptr;        // device: max nested iterations and residual of graph runs
 };
 
 // ------------------------------------------------------------------ launchers (aim.cu, near.cu)
@@ -251,6 +261,10 @@ sie_status csr_mv(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp, con
                   const double2* val, const double2* x, double2* y);
 sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, double* rcs);
 bool sys_z_workspace_ready(const sie_op* op);
+// drop the captured system-product graph (solver settings changed)
+void sys_graph_reset(sie_op* op);
+// fold the nested-solve statistics of graph runs into op->stats (synchronises)
+void sys_stats_fold(sie_op* op);
 sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int ndir, double2* sums);
 double sys_rcs_scale(const sie_op* op);
 // nbatch consecutive grids (buf + k n^3, src + k N^3) in one launch per pass

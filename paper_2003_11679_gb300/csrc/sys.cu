@@ -150,6 +150,8 @@ sie_status KrylovWork::alloc(cudaStream_t st, int64_t n_, int m_)
     SIE_CUDA_TRY(cudaMallocAsync((void**)&h, sizeof(double2) * 4 * (m + 2), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&part, sizeof(double2) * DOT_CHUNKS * (m + 1), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&cgsp, sizeof(double2) * CGS_CHUNKS * (2 * (m + 1) + 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&dv, sizeof(double2) * 2 * n, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&dj, sizeof(int) * 4, st));
     // Hessenberg (m+1) x m, rotations cs, sn, rhs g, solution y
     SIE_CUDA_TRY(cudaMallocAsync((void**)&Hd, sizeof(double2) * ((m + 1) * m + 2 * m + 2 * (m + 1)), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&sc, sizeof(double) * (8 + m + 1), st));
@@ -161,7 +163,9 @@ sie_status KrylovWork::alloc(cudaStream_t st, int64_t n_, int m_)
 
 void KrylovWork::release(cudaStream_t st)
 {
-    for (double2* p : {V, Z, w, h, r, part, cgsp, Hd})
+    if (dj) cudaFreeAsync(dj, st);
+    dj = nullptr;
+    for (double2* p : {V, Z, w, h, r, part, cgsp, dv, Hd})
         if (p) cudaFreeAsync(p, st);
     if (sc) cudaFreeAsync(sc, st);
     if (resid_h) {
@@ -170,7 +174,7 @@ void KrylovWork::release(cudaStream_t st)
     }
     for (auto& e : ev) cudaEventDestroy(e);
     ev.clear();
-    V = Z = w = h = r = part = cgsp = Hd = nullptr;
+    V = Z = w = h = r = part = cgsp = dv = Hd = nullptr;
     sc = nullptr;
     resid_h = nullptr;
     n = 0;
@@ -287,12 +291,20 @@ __device__ void cgs_partials(int64_t k0, int64_t k1, int nv, const double2* __re
     }
 }
 
-// pass 1: partial sums of V^H w
+// pass 1: partial sums of V^H w.  With jd (device-controlled iteration, jd[0]
+// = j) nv = j + 1 is read on the device and zsrc is stored as column j of Z.
 __global__ void __launch_bounds__(256) k_cgs_part(int64_t n, int nv, const double2* __restrict__ V, int64_t ld,
-                                                  const double2* __restrict__ w, double2* __restrict__ P, int ldp)
+                                                  const double2* __restrict__ w, double2* __restrict__ P, int ldp,
+                                                  const int* __restrict__ jd, const double2* __restrict__ zsrc,
+                                                  double2* __restrict__ Z)
 {
     int64_t k0, k1;
     cgs_rows(n, k0, k1);
+    if (jd) {
+        const int j = jd[0];
+        nv = j + 1;
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) Z[(int64_t)j * ld + k] = zsrc[k];
+    }
     cgs_partials(k0, k1, nv, V, ld, w, P, ldp);
 }
 
@@ -301,9 +313,11 @@ __global__ void __launch_bounds__(256) k_cgs_part(int64_t n, int nv, const doubl
 __global__ void __launch_bounds__(256) k_cgs_update(int64_t n, int nv, const double2* __restrict__ V, int64_t ld,
                                                     const double2* __restrict__ Pin, int ldp,
                                                     double2* __restrict__ hout, double2* __restrict__ w,
-                                                    double2* __restrict__ Pout, int last)
+                                                    double2* __restrict__ Pout, int last,
+                                                    const int* __restrict__ jd)
 {
     __shared__ double2 h[CGS_TILE];
+    if (jd) nv = jd[0] + 1;
     int64_t k0, k1;
     cgs_rows(n, k0, k1);
     for (int i0 = 0; i0 < nv; i0 += CGS_TILE) {
@@ -347,13 +361,16 @@ __global__ void __launch_bounds__(256) k_cgs_update(int64_t n, int nv, const dou
 
 // |w| = sqrt(sum_c P[c]); V_{j+1} = w / |w| on this chunk's rows; block 0
 // writes column j of H (h1 + h2 and |w|) and applies the Givens step
+// (V: the basis, column stride n; with jd, j = jd[0] is read on the device)
 __global__ void __launch_bounds__(256) k_cgs_finish(int64_t n, int j, int m, const double2* __restrict__ h1,
                                                     const double2* __restrict__ h2, const double2* __restrict__ P,
-                                                    const double2* __restrict__ w, double2* __restrict__ Vn,
+                                                    const double2* __restrict__ w, double2* __restrict__ V,
                                                     double2* __restrict__ H, double2* __restrict__ cs,
                                                     double2* __restrict__ sn, double2* __restrict__ g,
-                                                    double* __restrict__ sc)
+                                                    double* __restrict__ sc, const int* __restrict__ jd)
 {
+    if (jd) j = jd[0];
+    double2* Vn = V + (int64_t)(j + 1) * n;
     __shared__ double hn_s;
     if (threadIdx.x < 32) {
         double s = 0;
@@ -372,6 +389,72 @@ __global__ void __launch_bounds__(256) k_cgs_finish(int64_t n, int j, int m, con
     if (threadIdx.x == 0) H[(j + 1) * m + j] = make_double2(hn, 0);
     __syncthreads();
     if (threadIdx.x == 0) gm_givens(j, m, H, cs, sn, g, sc);
+}
+
+// ---- device-controlled cycle (the body of a CUDA-graph while loop).  jd[0]
+// is the iteration index j of the running cycle; jd[1] the iterations done.
+__global__ void k_gmd_init(int* __restrict__ jd)
+{
+    jd[0] = 0;
+    jd[1] = 0;
+}
+
+// vj = V[j]
+__global__ void k_gmd_fetch(int64_t n, const double2* __restrict__ V, const int* __restrict__ jd,
+                            double2* __restrict__ vj)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) vj[i] = V[(int64_t)jd[0] * n + i];
+}
+
+// after iteration j: continue while the relative residual sc[3 + j] is not
+// below tol and fewer than min(m, maxit) iterations ran (so the loop always ends)
+__global__ void k_gmd_cond(int* __restrict__ jd, const double* __restrict__ sc, double tol, int m, int maxit,
+                           cudaGraphConditionalHandle h)
+{
+    const int j = jd[0];
+    const bool more = sc[3 + j] >= tol && j + 1 < m && j + 1 < maxit;
+    jd[1] = j + 1;
+    if (more) jd[0] = j + 1;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// after the loop: jd[0] = last iteration jend; y = R^-1 g; out = (iterations, residual)
+__global__ void k_gmd_backsub(const int* __restrict__ jd, int m, const double2* __restrict__ H,
+                              const double2* __restrict__ g, double2* __restrict__ y, const double* __restrict__ sc,
+                              double* __restrict__ out)
+{
+    const int jend = jd[0];
+    for (int i = jend; i >= 0; i--) {
+        double2 s = g[i];
+        for (int k = i + 1; k <= jend; k++) {
+            double2 t = cm(H[i * m + k], y[k]);
+            s.x -= t.x;
+            s.y -= t.y;
+        }
+        double2 d = H[i * m + i];
+        double den = d.x * d.x + d.y * d.y;
+        y[i] = den > 0 ? make_double2((s.x * d.x + s.y * d.y) / den, (s.y * d.x - s.x * d.y) / den)
+                       : make_double2(0, 0);
+    }
+    out[0] = fmax(out[0], (double)jd[1]);
+    out[1] = fmax(out[1], sc[3 + jend]);
+}
+
+// x += Z[0..jend] y
+__global__ void k_gmd_update(int64_t n, const int* __restrict__ jd, const double2* __restrict__ Z,
+                             const double2* __restrict__ y, double2* __restrict__ x)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int nv = jd[0] + 1;
+    double sr = 0, si = 0;
+    for (int j = 0; j < nv; j++) {
+        double2 a = Z[(int64_t)j * n + k], b = y[j];
+        sr += a.x * b.x - a.y * b.y;
+        si += a.x * b.y + a.y * b.x;
+    }
+    x[k] = make_double2(x[k].x + sr, x[k].y + si);
 }
 
 // y = R^-1 g (upper triangular, size jend + 1)
@@ -434,11 +517,10 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
             double2* P1 = K.cgsp;
             double2* P2 = K.cgsp + (int64_t)CGS_CHUNKS * (m + 1);
             double2* P3 = K.cgsp + (int64_t)2 * CGS_CHUNKS * (m + 1);
-            k_cgs_part<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K.V, n, K.w, P1, m + 1);
-            k_cgs_update<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K.V, n, P1, m + 1, h1, K.w, P2, 0);
-            k_cgs_update<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K.V, n, P2, m + 1, h2, K.w, P3, 1);
-            k_cgs_finish<<<CGS_CHUNKS, 256, 0, st>>>(n, j, m, h1, h2, P3, K.w, K.V + (int64_t)(j + 1) * n, H, cs,
-                                                      sn, g, K.sc);
+            k_cgs_part<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K.V, n, K.w, P1, m + 1, nullptr, nullptr, nullptr);
+            k_cgs_update<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K.V, n, P1, m + 1, h1, K.w, P2, 0, nullptr);
+            k_cgs_update<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K.V, n, P2, m + 1, h2, K.w, P3, 1, nullptr);
+            k_cgs_finish<<<CGS_CHUNKS, 256, 0, st>>>(n, j, m, h1, h2, P3, K.w, K.V, H, cs, sn, g, K.sc, nullptr);
             SIE_CUDA_TRY(cudaGetLastError());
             SIE_CUDA_TRY(cudaMemcpyAsync(K.resid_h + j, K.sc + 3 + j, sizeof(double), cudaMemcpyDeviceToHost, st));
             SIE_CUDA_TRY(cudaEventRecord(K.ev[j], st));
@@ -475,6 +557,95 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
     if (iters_out) *iters_out = it;
     if (relres_out) *relres_out = rel;
     return rel < tol ? SIE_OK : SIE_ERR_NOT_CONVERGED;
+}
+
+// One FGMRES cycle (x0 = 0, at most min(m, maxit) iterations) emitted into the
+// stream c->stream while it is being captured into a CUDA graph: the
+// iterations form a conditional while node whose body ends with k_gmd_cond,
+// so the device decides when to stop and no host round trip is needed.  The
+// operators A and Minv are captured on the body stream body_st (c->stream is
+// switched to it while they run).  K must already be allocated for (n, m).
+// stat (device, 2 doubles) keeps the maximum iteration count and final
+// relative residual.  Same arithmetic as fgmres, without its lagged check.
+static sie_status fgmres_dev(sie_ctx* c, cudaStream_t body_st, KrylovWork& K, int64_t n, const Apply& A,
+                             const Apply& Minv, const double2* b, double2* x, double tol, int maxit, int m,
+                             double* stat)
+{
+    if (K.n != n || K.m != m) {
+        set_error("fgmres_dev: Krylov workspace not allocated");
+        return SIE_ERR_STATE;
+    }
+    cudaStream_t st = c->stream;
+    double2* H = K.Hd;
+    double2* cs = K.Hd + (m + 1) * m;
+    double2* sn = cs + m;
+    double2* g = sn + m;
+    double2* y = g + (m + 1);
+    double2* h1 = K.h;
+    double2* h2 = K.h + (m + 2);
+    double2* wd = K.h + 2 * (m + 2);
+    double2* vj = K.dv;
+    double2* zj = K.dv + n;
+    double2* P1 = K.cgsp;
+    double2* P2 = K.cgsp + (int64_t)CGS_CHUNKS * (m + 1);
+    double2* P3 = K.cgsp + (int64_t)2 * CGS_CHUNKS * (m + 1);
+    SIE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
+    SIE_TRY(dots(st, n, 1, b, n, b, K.part, wd));
+    k_gm_start<<<nb(n), 256, 0, st>>>(n, b, wd, K.V, g, m, K.sc, 1);
+    k_gmd_init<<<1, 1, 0, st>>>(K.dj);
+    SIE_CUDA_TRY(cudaGetLastError());
+    // while node after the current capture frontier
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    SIE_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, &deps, &edges, &ndeps));
+    if (cst != cudaStreamCaptureStatusActive) {
+        set_error("fgmres_dev: stream is not being captured");
+        return SIE_ERR_STATE;
+    }
+    cudaGraphConditionalHandle hc;
+    SIE_CUDA_TRY(cudaGraphConditionalHandleCreate(&hc, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};  // the rest zero
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    SIE_CUDA_TRY(cudaGraphAddNode(&wnode, graph, deps, edges, ndeps, &cp));
+    SIE_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // body: one Arnoldi step
+    SIE_CUDA_TRY(cudaStreamBeginCaptureToGraph(body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c->stream = body_st;
+    sie_status s = SIE_OK;
+    do {
+        k_gmd_fetch<<<nb(n), 256, 0, body_st>>>(n, K.V, K.dj, vj);
+        if ((s = Minv(vj, zj)) != SIE_OK) break;
+        if ((s = A(zj, K.w)) != SIE_OK) break;
+        k_cgs_part<<<CGS_CHUNKS, 256, 0, body_st>>>(n, 0, K.V, n, K.w, P1, m + 1, K.dj, zj, K.Z);
+        k_cgs_update<<<CGS_CHUNKS, 256, 0, body_st>>>(n, 0, K.V, n, P1, m + 1, h1, K.w, P2, 0, K.dj);
+        k_cgs_update<<<CGS_CHUNKS, 256, 0, body_st>>>(n, 0, K.V, n, P2, m + 1, h2, K.w, P3, 1, K.dj);
+        k_cgs_finish<<<CGS_CHUNKS, 256, 0, body_st>>>(n, 0, m, h1, h2, P3, K.w, K.V, H, cs, sn, g, K.sc, K.dj);
+        k_gmd_cond<<<1, 1, 0, body_st>>>(K.dj, K.sc, tol, m, maxit, hc);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error(std::string("fgmres_dev: ") + cudaGetErrorString(e));
+            s = SIE_ERR_CUDA;
+        }
+    } while (0);
+    c->stream = st;
+    cudaGraph_t tmp = nullptr;
+    cudaError_t e = cudaStreamEndCapture(body_st, &tmp);
+    if (s != SIE_OK) return s;
+    if (e != cudaSuccess) {
+        set_error(std::string("fgmres_dev: body capture: ") + cudaGetErrorString(e));
+        return SIE_ERR_CUDA;
+    }
+    k_gmd_backsub<<<1, 1, 0, st>>>(K.dj, m, H, g, y, K.sc, stat);
+    k_gmd_update<<<nb(n), 256, 0, st>>>(n, K.dj, K.Z, y, x);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
 }
 
 // ------------------------------------------------------------------ system kernels
@@ -975,21 +1146,27 @@ static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_i
     } else {
         Minv = [&](const double2* x, double2* y) {
             Stage s_(c, "spai_apply");
-            return csr_mv(st, (int)ne, I.nnz, I.row_ptr, I.col, I.valM, x, y);
+            return csr_mv(c->stream, (int)ne, I.nnz, I.row_ptr, I.col, I.valM, x, y);
         };
     }
-    int it = 0;
-    double rr = 0;
-    sie_status s;
-    {
-        Stage s_(c, "inner_solve");
-        s = fgmres(c, op->kin, ne, A, Minv, a, E, op->p.tol_inner, op->p.inner_maxit, std::min(op->p.restart, 60),
-                   &it, &rr);
+    const int m_in = std::min(op->p.restart, 60);
+    if (op->capturing && !I.has_grid) {
+        // inside the system-product graph: device-controlled nested cycle
+        SIE_TRY(fgmres_dev(c, op->gs[1], op->kin, ne, A, Minv, a, E, op->p.tol_inner, op->p.inner_maxit, m_in,
+                           op->gstat));
+    } else {
+        int it = 0;
+        double rr = 0;
+        sie_status s;
+        {
+            Stage s_(c, "inner_solve");
+            s = fgmres(c, op->kin, ne, A, Minv, a, E, op->p.tol_inner, op->p.inner_maxit, m_in, &it, &rr);
+        }
+        if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
+        if (inner_iters) *inner_iters = it;
+        op->stats[2] = std::max(op->stats[2], (double)it);
+        op->stats[3] = std::max(op->stats[3], rr);
     }
-    if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
-    if (inner_iters) *inner_iters = it;
-    op->stats[2] = std::max(op->stats[2], (double)it);
-    op->stats[3] = std::max(op->stats[3], rr);
     cplx zs(0.0, op->k0 * op->eps_r);
     zs += op->sigma * ETA0;
     SIE_TRY(axpby(st, ne, -1.0 / zs, E, 0.0, E));
@@ -1086,6 +1263,92 @@ static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
         SIE_CUDA_TRY(cudaGetLastError());
     }
     return SIE_OK;
+}
+
+// ------------------------------------------------------------------ graph of the system product
+// For a near-region-only interior the whole product (nested solve included)
+// is captured once into a CUDA graph: one launch per product instead of ~80,
+// and the nested iteration count is decided on the device.  One graph per
+// precision; dropped when the nested-solve settings change.  SIE_GRAPH=0 in the
+// environment keeps the stream path (for comparison).
+static bool graph_enabled()
+{
+    const char* e = getenv("SIE_GRAPH");
+    return !(e && e[0] == '0');
+}
+
+void sys_graph_reset(sie_op* op)
+{
+    for (cudaGraphExec_t& g : op->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    op->gfailed = false;
+}
+
+static sie_status build_sys_graph(sie_op* op)
+{
+    sie_ctx* c = op->mesh->ctx;
+    const int64_t ne = op->mesh->h.ne, n = ne + op->mesh->h.nt;
+    // everything the product touches exists before the capture starts
+    SIE_TRY(op->kin.alloc(c->stream, ne, std::min(op->p.restart, 60)));
+    if (!op->g_io) SIE_CUDA_TRY(cudaMallocAsync((void**)&op->g_io, sizeof(double2) * 2 * n, c->stream));
+    if (!op->gstat) {
+        SIE_CUDA_TRY(cudaMallocAsync((void**)&op->gstat, sizeof(double) * 2, c->stream));
+        SIE_CUDA_TRY(cudaMemsetAsync(op->gstat, 0, sizeof(double) * 2, c->stream));
+    }
+    for (int i = 0; i < 2; i++)
+        if (!op->gs[i]) SIE_CUDA_TRY(cudaStreamCreateWithFlags(&op->gs[i], cudaStreamNonBlocking));
+    SIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    cudaStream_t saved = c->stream;
+    c->stream = op->gs[0];
+    op->capturing = true;
+    cudaGraph_t graph = nullptr;
+    sie_status s = SIE_OK;
+    cudaError_t e = cudaStreamBeginCapture(op->gs[0], cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        s = apply_sys(op, op->g_io, op->g_io + n);
+        cudaError_t e2 = cudaStreamEndCapture(op->gs[0], &graph);
+        if (s == SIE_OK) e = e2;
+    }
+    op->capturing = false;
+    c->stream = saved;
+    cudaGraphExec_t& gx = op->gexec[op->p.precision == SIE_MIXED ? 1 : 0];
+    if (s == SIE_OK && e == cudaSuccess) e = cudaGraphInstantiate(&gx, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (s != SIE_OK || e != cudaSuccess) {
+        if (gx) cudaGraphExecDestroy(gx);
+        gx = nullptr;
+        op->gfailed = true;
+        if (e != cudaSuccess) set_error(std::string("system-product graph: ") + cudaGetErrorString(e));
+        return s != SIE_OK ? s : SIE_ERR_CUDA;
+    }
+    return SIE_OK;
+}
+
+// y = SYS x through the graph when it applies, else the stream path
+static sie_status apply_sys_fast(sie_op* op, const double2* x, double2* y)
+{
+    sie_ctx* c = op->mesh->ctx;
+    if (op->inn.has_grid || c->prof.on || op->gfailed || !graph_enabled()) return apply_sys(op, x, y);
+    cudaGraphExec_t& gx = op->gexec[op->p.precision == SIE_MIXED ? 1 : 0];
+    if (!gx && build_sys_graph(op) != SIE_OK) return apply_sys(op, x, y);
+    const int64_t n = op->mesh->h.ne + op->mesh->h.nt;
+    SIE_CUDA_TRY(cudaMemcpyAsync(op->g_io, x, sizeof(double2) * n, cudaMemcpyDeviceToDevice, c->stream));
+    SIE_CUDA_TRY(cudaGraphLaunch(gx, c->stream));
+    SIE_CUDA_TRY(cudaMemcpyAsync(y, op->g_io + n, sizeof(double2) * n, cudaMemcpyDeviceToDevice, c->stream));
+    return SIE_OK;
+}
+
+void sys_stats_fold(sie_op* op)
+{
+    if (!op->gstat) return;
+    double h[2] = {0, 0};
+    cudaStream_t st = op->mesh->ctx->stream;
+    if (cudaMemcpyAsync(h, op->gstat, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return;
+    op->stats[2] = std::max(op->stats[2], h[0]);
+    op->stats[3] = std::max(op->stats[3], h[1]);
 }
 
 // Constraint preconditioner (the near-region form of the AEFIE constraint
@@ -1241,6 +1504,16 @@ sie_status sys_prepare(sie_op* op)
 void sys_release(sie_op* op)
 {
     cudaStream_t st = op->mesh->ctx->stream;
+    sys_graph_reset(op);
+    for (cudaStream_t& g : op->gs)
+        if (g) {
+            cudaStreamDestroy(g);
+            g = nullptr;
+        }
+    if (op->g_io) cudaFreeAsync(op->g_io, st);
+    if (op->gstat) cudaFreeAsync(op->gstat, st);
+    op->g_io = nullptr;
+    op->gstat = nullptr;
     op->kin.release(st);
     op->kout.release(st);
     op->kcs_in.release(st);
@@ -1254,16 +1527,17 @@ void sys_release(sie_op* op)
 
 sie_status sys_matvec(sie_op* op, int which, const double2* x, double2* y)
 {
-    if (which == SIE_OP_SYS) return apply_sys(op, x, y);
+    if (which == SIE_OP_SYS) return apply_sys_fast(op, x, y);
     return apply_Z(op, x, y, nullptr);
 }
 
 sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres)
 {
     const int64_t n = op->mesh->h.ne + op->mesh->h.nt;
-    Apply A = [&](const double2* u, double2* v) { return apply_sys(op, u, v); };
+    Apply A = [&](const double2* u, double2* v) { return apply_sys_fast(op, u, v); };
     Apply Minv = [&](const double2* u, double2* v) { return precond_sys(op, u, v); };
     for (int i = 2; i < 6; i++) op->stats[i] = 0;
+    if (op->gstat) SIE_CUDA_TRY(cudaMemsetAsync(op->gstat, 0, sizeof(double) * 2, op->mesh->ctx->stream));
     int it = 0;
     double rr = 0;
     sie_status s = fgmres(op->mesh->ctx, op->kout, n, A, Minv, b, x, op->p.tol_outer, op->p.maxit, op->p.restart,
