@@ -176,7 +176,10 @@ sie_status sie_op_stats(const sie_op* op, double out[6]);
  * in ms: [12] weights and spectra, [13] exterior near region, [14] interior
  * near region, [15] host-side pair lists; [16] system-product CUDA graph
  * (near-region-only interiors): +1 captured for SIE_FP64, +2 for SIE_MIXED,
- * +4 capture failed (the stream path is used); [17..19] reserved (0). */
+ * +4 capture failed (the stream path is used); [17] nodes of the last
+ * captured graph outside the nested loop (kernels, memsets, copies and the
+ * loop node), [18] nodes of the loop body (run once per nested iteration);
+ * [19] reserved (0). */
 sie_status sie_op_info(const sie_op* op, double info[20]);
 /* grid origin (3) and spacing of the exterior grid */
 sie_status sie_op_grid(const sie_op* op, double origin[3], double* h, int64_t N[3]);

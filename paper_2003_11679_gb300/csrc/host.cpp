@@ -550,7 +550,9 @@ sie_status sie_op_info(const sie_op* op, double info[20])
     info[11] = g.o[0];
     for (int i = 0; i < 4; i++) info[12 + i] = op->build_ms[i];
     info[16] = (op->gexec[0] ? 1.0 : 0.0) + (op->gexec[1] ? 2.0 : 0.0) + (op->gfailed ? 4.0 : 0.0);
-    for (int i = 17; i < 20; i++) info[i] = 0.0;
+    info[17] = (double)op->gnodes[0];
+    info[18] = (double)op->gnodes[1];
+    info[19] = 0.0;
     return SIE_OK;
 }
 

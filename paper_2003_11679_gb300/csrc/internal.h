@@ -240,6 +240,7 @@ struct sie_op {
     cudaStream_t gs[2] = {nullptr, nullptr};  // capture streams: graph, while-loop body
     double2* g_io = nullptr;        // graph input x and output y, 2 (ne + nt)
     double* gstat = nullptr;        // device: max nested iterations and residual of graph runs
+    size_t gnodes[2] = {0, 0};      // nodes of the last captured graph: outside the loop, loop body
 };
 
 // ------------------------------------------------------------------ launchers (aim.cu, near.cu)

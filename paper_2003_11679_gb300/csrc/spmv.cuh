@@ -18,7 +18,7 @@ __device__ __forceinline__ double2 csr_row_dot(int64_t e0, int64_t e1, const int
                                                const VT* __restrict__ val, const double2* __restrict__ x, int l)
 {
     using R = decltype(VT{}.x);
-    R ar = 0, ai = 0;
+    R ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};  // one set per unrolled slot (independent chains)
     int64_t e = e0 + l;
     for (; e + 3 * G < e1; e += 4 * G) {
         int c[4];
@@ -34,18 +34,19 @@ __device__ __forceinline__ double2 csr_row_dot(int64_t e0, int64_t e1, const int
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const R xr = (R)xv[u].x, xi = (R)xv[u].y;
-            ar += v[u].x * xr - v[u].y * xi;
-            ai += v[u].x * xi + v[u].y * xr;
+            ar[u] += v[u].x * xr - v[u].y * xi;
+            ai[u] += v[u].x * xi + v[u].y * xr;
         }
     }
-    for (; e < e1; e += G) {
+    for (; e < e1; e += G) {  // at most 3 more entries per lane
         VT v = __ldg(val + e);
         double2 xd = __ldg(x + __ldg(col + e));
         const R xr = (R)xd.x, xi = (R)xd.y;
-        ar += v.x * xr - v.y * xi;
-        ai += v.x * xi + v.y * xr;
+        ar[0] += v.x * xr - v.y * xi;
+        ai[0] += v.x * xi + v.y * xr;
     }
-    double sr = ar, si = ai;
+    double sr = ((double)ar[0] + (double)ar[1]) + ((double)ar[2] + (double)ar[3]);
+    double si = ((double)ai[0] + (double)ai[1]) + ((double)ai[2] + (double)ai[3]);
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
         sr += __shfl_xor_sync(0xffffffffu, sr, off);

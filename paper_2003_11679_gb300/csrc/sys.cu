@@ -569,7 +569,7 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
 // relative residual.  Same arithmetic as fgmres, without its lagged check.
 static sie_status fgmres_dev(sie_ctx* c, cudaStream_t body_st, KrylovWork& K, int64_t n, const Apply& A,
                              const Apply& Minv, const double2* b, double2* x, double tol, int maxit, int m,
-                             double* stat)
+                             double* stat, size_t* body_nodes)
 {
     if (K.n != n || K.m != m) {
         set_error("fgmres_dev: Krylov workspace not allocated");
@@ -642,6 +642,7 @@ static sie_status fgmres_dev(sie_ctx* c, cudaStream_t body_st, KrylovWork& K, in
         set_error(std::string("fgmres_dev: body capture: ") + cudaGetErrorString(e));
         return SIE_ERR_CUDA;
     }
+    if (body_nodes) SIE_CUDA_TRY(cudaGraphGetNodes(body, nullptr, body_nodes));
     k_gmd_backsub<<<1, 1, 0, st>>>(K.dj, m, H, g, y, K.sc, stat);
     k_gmd_update<<<nb(n), 256, 0, st>>>(n, K.dj, K.Z, y, x);
     SIE_CUDA_TRY(cudaGetLastError());
@@ -891,7 +892,8 @@ __global__ void __launch_bounds__(128) k_spmv2(int nrow, const int64_t* __restri
     int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (r >= nrow) return;
-    double s1r = 0, s1i = 0, s2r = 0, s2i = 0;
+    // one accumulator set per unrolled slot: 16 independent FP64 FMA chains
+    double s1r[4] = {0, 0, 0, 0}, s1i[4] = {0, 0, 0, 0}, s2r[4] = {0, 0, 0, 0}, s2i[4] = {0, 0, 0, 0};
     const int64_t e0 = rp[r], e1 = rp[r + 1];
     int64_t e = e0 + lane;
     for (; e + 96 < e1; e += 128) {
@@ -907,29 +909,31 @@ __global__ void __launch_bounds__(128) k_spmv2(int nrow, const int64_t* __restri
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             double2 xa = __ldg(x1 + c[u]), xb = __ldg(x2 + c[u]);
-            s1r += p[u].x * xa.x - p[u].y * xa.y;
-            s1i += p[u].x * xa.y + p[u].y * xa.x;
-            s2r += q[u].x * xb.x - q[u].y * xb.y;
-            s2i += q[u].x * xb.y + q[u].y * xb.x;
+            s1r[u] += p[u].x * xa.x - p[u].y * xa.y;
+            s1i[u] += p[u].x * xa.y + p[u].y * xa.x;
+            s2r[u] += q[u].x * xb.x - q[u].y * xb.y;
+            s2i[u] += q[u].x * xb.y + q[u].y * xb.x;
         }
     }
-    for (; e < e1; e += 32) {
+    for (; e < e1; e += 32) {  // at most 3 more entries per lane
         int c = col[e];
         double2 p = v1[e], q = v2[e], xa = x1[c], xb = x2[c];
-        s1r += p.x * xa.x - p.y * xa.y;
-        s1i += p.x * xa.y + p.y * xa.x;
-        s2r += q.x * xb.x - q.y * xb.y;
-        s2i += q.x * xb.y + q.y * xb.x;
+        s1r[0] += p.x * xa.x - p.y * xa.y;
+        s1i[0] += p.x * xa.y + p.y * xa.x;
+        s2r[0] += q.x * xb.x - q.y * xb.y;
+        s2i[0] += q.x * xb.y + q.y * xb.x;
     }
+    double t1r = (s1r[0] + s1r[1]) + (s1r[2] + s1r[3]), t1i = (s1i[0] + s1i[1]) + (s1i[2] + s1i[3]);
+    double t2r = (s2r[0] + s2r[1]) + (s2r[2] + s2r[3]), t2i = (s2i[0] + s2i[1]) + (s2i[2] + s2i[3]);
     for (int off = 16; off > 0; off >>= 1) {
-        s1r += __shfl_down_sync(0xffffffffu, s1r, off);
-        s1i += __shfl_down_sync(0xffffffffu, s1i, off);
-        s2r += __shfl_down_sync(0xffffffffu, s2r, off);
-        s2i += __shfl_down_sync(0xffffffffu, s2i, off);
+        t1r += __shfl_down_sync(0xffffffffu, t1r, off);
+        t1i += __shfl_down_sync(0xffffffffu, t1i, off);
+        t2r += __shfl_down_sync(0xffffffffu, t2r, off);
+        t2i += __shfl_down_sync(0xffffffffu, t2i, off);
     }
     if (lane == 0) {
-        y[r].x += a1.x * s1r - a1.y * s1i + a2.x * s2r - a2.y * s2i;
-        y[r].y += a1.x * s1i + a1.y * s1r + a2.x * s2i + a2.y * s2r;
+        y[r].x += a1.x * t1r - a1.y * t1i + a2.x * t2r - a2.y * t2i;
+        y[r].y += a1.x * t1i + a1.y * t1r + a2.x * t2i + a2.y * t2r;
     }
 }
 
@@ -1153,7 +1157,7 @@ static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_i
     if (op->capturing && !I.has_grid) {
         // inside the system-product graph: device-controlled nested cycle
         SIE_TRY(fgmres_dev(c, op->gs[1], op->kin, ne, A, Minv, a, E, op->p.tol_inner, op->p.inner_maxit, m_in,
-                           op->gstat));
+                           op->gstat, &op->gnodes[1]));
     } else {
         int it = 0;
         double rr = 0;
@@ -1314,6 +1318,7 @@ static sie_status build_sys_graph(sie_op* op)
     op->capturing = false;
     c->stream = saved;
     cudaGraphExec_t& gx = op->gexec[op->p.precision == SIE_MIXED ? 1 : 0];
+    if (s == SIE_OK && e == cudaSuccess) e = cudaGraphGetNodes(graph, nullptr, &op->gnodes[0]);
     if (s == SIE_OK && e == cudaSuccess) e = cudaGraphInstantiate(&gx, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (s != SIE_OK || e != cudaSuccess) {
