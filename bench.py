@@ -58,6 +58,24 @@ def dist_env():
     return rank, world, local
 
 
+def combine_ranks(ms, e2e_s, world, device):
+    """Whole-job times of a replicas run: the slowest rank sets them (max over
+    ranks of the timed-region milliseconds and of the end-to-end seconds)."""
+    if world == 1:
+        return ms, e2e_s
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, e2e_s], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0]), float(t[1])
+
+
+def job_value(world, ne, steps, ms):
+    """RWG unknowns x system matvecs per second over all ranks (each rank runs
+    its own replica of the workload)."""
+    return world * ne * steps / (ms * 1e-3)
+
+
 class Clocks:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -204,6 +222,8 @@ def run_ours(args):
 
         with Clocks(local) as clk:
             ms, _ = timed(False, "sie_fp64")  # the reported step time: no stage events
+            if world > 1:
+                dist.barrier()
             ginfo, gstats = op.info(), op.stats()  # graph nodes and nested iterations of the timed loop
             ms_prof, prof = timed(True)     # stage breakdown and roofline kernel times
         nested = op.stats()
@@ -233,13 +253,10 @@ def run_ours(args):
         # current rows (the grid product lives there; the charge rows are exact in both)
         mixed_err = float((y[:ne] - y64[:ne]).abs().norm() / y64[:ne].abs().norm())
     solves = solve_stats(sie, ctx, args) if not args.no_solve else None
-    if world > 1:
-        t = torch.tensor([ms, e2e_s], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
+    ms, e2e_s = combine_ranks(ms, e2e_s, world, f"cuda:{local}")
     if rank != 0:
         return
-    value = world * ne * args.steps / (ms * 1e-3)
+    value = job_value(world, ne, args.steps, ms)
     peaks, kind = measured_peaks()
     # dominant kernel stage (solver bookkeeping stages excluded) and its roofline
     kern = {k: v for k, v in prof.items() if k not in ("inner_solve", "constraint_solve")}
@@ -268,7 +285,7 @@ def run_ours(args):
         launches = args.steps * int(ginfo[17] + ginfo[18] * gstats["inner_iters_max"])
     else:
         launches = sum(c for _, c in prof.values())
-    cpu = cpu_baseline(wl, args) if not args.no_cpu else None
+    cpu = cpu_baseline(wl, args) if not args.no_cpu and world == 1 else None  # rank 0 at N = 1 only
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -278,7 +295,7 @@ def run_ours(args):
                    "near_nnz_int": int(nnz_int), "step": "system matvec, Eq. (sys) (AEFIE, [H; c0 rho])",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
                    "build_s": build_s, "build_ms_breakdown": info[12:16].tolist()},
-        "e2e": {"value": world * ne * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * 16,
+        "e2e": {"value": job_value(world, ne, args.steps, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": n * 16,
                 "d2h_bytes_per_step": n * 16},
         "gpu_launches": launches,
         "ms_per_step_with_stage_events": ms_prof / args.steps,
