@@ -1283,6 +1283,8 @@ static bool graph_enabled()
 
 void sys_graph_reset(sie_op* op)
 {
+    // a replay may still be queued on the context stream
+    if (op->gexec[0] || op->gexec[1]) cudaStreamSynchronize(op->mesh->ctx->stream);
     for (cudaGraphExec_t& g : op->gexec) {
         if (g) cudaGraphExecDestroy(g);
         g = nullptr;
