@@ -11,6 +11,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 #include "spmv.cuh"
@@ -144,46 +145,59 @@ sie_status aim_weights(sie_op* op)
 }
 
 // ------------------------------------------------------------------ FFT
-// Twiddles exp(-2 pi i k / n), k < n, for n = 2^l (l <= 10).
-static double2* g_tw[11] = {nullptr};
-static float2* g_tw32[11] = {nullptr};
-static int g_tw_dev[11] = {-1};
+// Twiddles exp(-2 pi i k / n), k < n, for n = 2^l (l <= 10): one table per
+// device and length, made on first use (guarded: contexts may run in threads).
+constexpr int TW_MAXDEV = 64;
+static double2* g_tw[TW_MAXDEV][11] = {};
+static float2* g_tw32[TW_MAXDEV][11] = {};
+static std::mutex g_tw_mu;
 
-static sie_status twiddles(int logn, cudaStream_t st, double2** out)
+static sie_status twiddles_dev(int logn, int dev, double2** out, float2** out32)
 {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (g_tw[logn] && g_tw_dev[logn] == dev) {
-        *out = g_tw[logn];
-        return SIE_OK;
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    if (!g_tw[dev][logn]) {
+        int n = 1 << logn;
+        std::vector<double2> h(std::max(n, 1));
+        for (int k = 0; k < n; k++) {
+            long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)n;
+            h[k] = make_double2((double)cosl(a), (double)sinl(a));
+        }
+        double2* d = nullptr;
+        SIE_CUDA_TRY(cudaMalloc((void**)&d, sizeof(double2) * h.size()));
+        SIE_CUDA_TRY(cudaMemcpy(d, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice));
+        std::vector<float2> hf(h.size());
+        for (size_t k = 0; k < h.size(); k++) hf[k] = make_float2((float)h[k].x, (float)h[k].y);
+        float2* f = nullptr;
+        SIE_CUDA_TRY(cudaMalloc((void**)&f, sizeof(float2) * hf.size()));
+        SIE_CUDA_TRY(cudaMemcpy(f, hf.data(), sizeof(float2) * hf.size(), cudaMemcpyHostToDevice));
+        g_tw[dev][logn] = d;
+        g_tw32[dev][logn] = f;
     }
-    int n = 1 << logn;
-    std::vector<double2> h(std::max(n, 1));
-    for (int k = 0; k < n; k++) {
-        long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)n;
-        h[k] = make_double2((double)cosl(a), (double)sinl(a));
-    }
-    double2* d = nullptr;
-    SIE_CUDA_TRY(cudaMalloc((void**)&d, sizeof(double2) * h.size()));
-    SIE_CUDA_TRY(cudaMemcpy(d, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice));
-    std::vector<float2> hf(h.size());
-    for (size_t k = 0; k < h.size(); k++) hf[k] = make_float2((float)h[k].x, (float)h[k].y);
-    float2* f = nullptr;
-    SIE_CUDA_TRY(cudaMalloc((void**)&f, sizeof(float2) * hf.size()));
-    SIE_CUDA_TRY(cudaMemcpy(f, hf.data(), sizeof(float2) * hf.size(), cudaMemcpyHostToDevice));
-    g_tw[logn] = d;
-    g_tw32[logn] = f;
-    g_tw_dev[logn] = dev;
-    *out = d;
+    if (out) *out = g_tw[dev][logn];
+    if (out32) *out32 = g_tw32[dev][logn];
     return SIE_OK;
 }
 
-static sie_status twiddles(int logn, cudaStream_t st, float2** out)
+static sie_status twiddles(int logn, cudaStream_t, double2** out)
 {
-    double2* d = nullptr;
-    SIE_TRY(twiddles(logn, st, &d));
-    *out = g_tw32[logn];
-    return SIE_OK;
+    int dev = 0;
+    SIE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= TW_MAXDEV) {
+        set_error("twiddles: device ordinal out of range");
+        return SIE_ERR_ARG;
+    }
+    return twiddles_dev(logn, dev, out, nullptr);
+}
+
+static sie_status twiddles(int logn, cudaStream_t, float2** out)
+{
+    int dev = 0;
+    SIE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= TW_MAXDEV) {
+        set_error("twiddles: device ordinal out of range");
+        return SIE_ERR_ARG;
+    }
+    return twiddles_dev(logn, dev, nullptr, out);
 }
 
 struct PassGeom {
@@ -532,11 +546,10 @@ static sie_status launch_pass_pb(cudaStream_t st, const C* in, C* out, int inv, 
 {
     constexpr int n = 1 << LOGN;
     size_t smem = sizeof(C) * PB * (n + 1);
-    static bool attr = false;
-    if (!attr) {
-        SIE_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<LOGN, PB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    // once per instantiation (thread-safe static initialisation)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_fft_pass<LOGN, PB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    SIE_CUDA_TRY(attr);
     unsigned blocks = (unsigned)((G.npencil + PB - 1) / PB);
     k_fft_pass<LOGN, PB, C><<<dim3(blocks, nbatch), 256, smem, st>>>(in, out, tw, inv, G);
     SIE_CUDA_TRY(cudaGetLastError());
@@ -574,14 +587,15 @@ static sie_status launch_stockham(cudaStream_t st, const C* in, C* out, int inv,
 {
     constexpr int n = 1 << LOGN;
     size_t smem = sizeof(C) * 2 * PB * (n + 1);
-    static bool attr = false;
-    if (!attr) {
-        SIE_CUDA_TRY(cudaFuncSetAttribute(k_fft_stockham<LOGN, PB, C, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        SIE_CUDA_TRY(cudaFuncSetAttribute(k_fft_stockham<LOGN, PB, C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        attr = true;
-    }
+    // once per instantiation (thread-safe static initialisation)
+    static const cudaError_t attr = [smem] {
+        cudaError_t e = cudaFuncSetAttribute(k_fft_stockham<LOGN, PB, C, 0>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_fft_stockham<LOGN, PB, C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    }();
+    SIE_CUDA_TRY(attr);
     unsigned blocks = (unsigned)((G.npencil + PB - 1) / PB);
     constexpr int threads = PB * n / 8;
     if (inv)

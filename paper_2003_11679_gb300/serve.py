@@ -1,0 +1,264 @@
+"""Request loop over the C ABI: GIBC scattering solves of different meshes,
+materials and frequencies admitted into concurrent slots.
+
+* A request is a closed mesh (V, T), a frequency, a material (eps_r, sigma), a
+  plane wave (khat, epol) and observation directions; its answer is the RCS in
+  those directions with the solve's iteration count and residual.
+* Slots: each slot is a worker thread with its own library context on its own
+  CUDA stream, so requests in different slots run on the GPU at the same time.
+  A request that arrives while every slot is busy waits in the queue and is
+  admitted as soon as any slot frees up (continuous admission, no batch
+  boundaries).
+* Resident state: the operator of a (mesh, frequency, material) key -- kernel
+  spectra, near-region matrices, Krylov bases, the captured system-product
+  graph -- stays on the device in the slot that built it and serves later
+  requests with the same key.
+* Device memory: before a slot builds an operator it needs free device memory
+  of at least the reserve (10% of the device by default) plus an estimate of
+  the operator's size (bytes per RWG unknown, the largest ratio measured so
+  far); it first releases its own least recently used operators, then waits
+  for other slots to finish; a request that cannot fit with every other slot
+  idle and its own cache empty fails with MemoryError.
+* Latency: per request, from submit to answer (queue + build + solve + RCS);
+  stats() reports p50 / p99 and the counters.
+
+The backend is pluggable so that the admission logic can be exercised without
+a GPU; LibraryBackend drives the library.
+"""
+import collections
+import concurrent.futures
+import hashlib
+import threading
+import time
+
+import numpy as np
+
+
+class Request:
+    """One scattering solve.  params: extra sie_params fields (e.g. tol_outer)."""
+
+    def __init__(self, V, T, freq, eps_r, sigma, khat, epol, rhat, params=None):
+        self.V = np.ascontiguousarray(V, dtype=np.float64)
+        self.T = np.ascontiguousarray(T, dtype=np.int32)
+        self.freq, self.eps_r, self.sigma = float(freq), float(eps_r), float(sigma)
+        self.khat = np.asarray(khat, float)
+        self.epol = np.asarray(epol, float)
+        self.rhat = np.atleast_2d(np.asarray(rhat, float))
+        self.params = dict(params or {})
+        self.ne = 3 * len(self.T) // 2
+
+    def key(self):
+        """Operators are shared by requests with the same mesh, frequency,
+        material and operator parameters."""
+        h = hashlib.sha1(self.V.tobytes())
+        h.update(self.T.tobytes())
+        h.update(repr((self.freq, self.eps_r, self.sigma, sorted(self.params.items()))).encode())
+        return h.hexdigest()
+
+
+class LibraryBackend:
+    """A slot's binding to the library: one context on its own CUDA stream
+    (created with torch, which only provides the stream and the memory query)."""
+
+    def __init__(self, device=0):
+        import torch
+
+        from . import Context
+        self.device = device
+        self.stream = torch.cuda.Stream(device=device)
+        self.ctx = Context(device, stream=self.stream.cuda_stream)
+
+    def build(self, req):
+        from . import Mesh, Operator, params
+        mesh = Mesh(self.ctx, req.V, req.T)
+        try:
+            op = Operator(mesh, req.freq, req.eps_r, 1.0, req.sigma, params(**req.params))
+        except Exception:
+            mesh.close()
+            raise
+        return (mesh, op)
+
+    def run(self, handle, req):
+        _, op = handle
+        b = op.rhs_planewave(req.khat, req.epol)
+        x, it, rr = op.solve(b, check=False)
+        rcs = op.rcs(x, req.rhat)
+        return {"rcs": rcs, "iters": int(it[0]), "relres": float(rr[0])}
+
+    def release(self, handle):
+        mesh, op = handle
+        op.close()
+        mesh.close()
+
+    def memory(self):
+        """(free, total) device bytes."""
+        import torch
+        return torch.cuda.mem_get_info(self.device)
+
+    def close(self):
+        self.ctx.close()
+
+
+class Server:
+    """Slots, queue, resident operators and memory admission (module docstring)."""
+
+    def __init__(self, slots=2, backend_factory=None, reserve_fraction=0.10, bytes_per_unknown=128 * 1024,
+                 wait_s=0.05):
+        self.backend_factory = backend_factory or (lambda slot: LibraryBackend(0))
+        self.reserve_fraction = reserve_fraction
+        self.bytes_per_unknown = float(bytes_per_unknown)   # estimate, raised by measured builds
+        self.wait_s = wait_s
+        self._cv = threading.Condition()
+        self._queue = collections.deque()
+        self._busy = 0
+        self._closed = False
+        self._lat = []
+        self._measured = 0.0          # largest measured operator bytes per RWG unknown
+        self.counters = collections.Counter()
+        self._build_lock = threading.Lock()   # one operator set-up at a time
+        self._backends = [None] * slots
+        self._caches = [collections.OrderedDict() for _ in range(slots)]  # key -> handle, LRU first
+        self._slot_locks = [threading.Lock() for _ in range(slots)]       # held while a slot serves
+        self._init_errors = []
+        self._threads = [threading.Thread(target=self._loop, args=(s,), daemon=True) for s in range(slots)]
+        self._ready = threading.Barrier(slots + 1)
+        for t in self._threads:
+            t.start()
+        self._ready.wait()
+        if self._init_errors:
+            self.close()
+            raise self._init_errors[0]
+
+    # ---------------------------------------------------------------- public
+    def submit(self, req):
+        fut = concurrent.futures.Future()
+        with self._cv:
+            if self._closed:
+                raise RuntimeError("server closed")
+            self._queue.append((req, fut, time.perf_counter()))
+            self._cv.notify_all()
+        return fut
+
+    def stats(self):
+        with self._cv:
+            lat = np.array(self._lat)
+            out = dict(self.counters)
+        out["completed"] = int(len(lat))
+        if len(lat):
+            out["p50_s"] = float(np.percentile(lat, 50))
+            out["p99_s"] = float(np.percentile(lat, 99))
+        out["bytes_per_unknown"] = self._estimate_per_unknown()
+        return out
+
+    def close(self):
+        with self._cv:
+            self._closed = True
+            self._cv.notify_all()
+        for t in self._threads:
+            t.join()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- slots
+    def _estimate_per_unknown(self):
+        return self._measured if self._measured > 0 else self.bytes_per_unknown
+
+    def _loop(self, slot):
+        try:
+            self._backends[slot] = self.backend_factory(slot)  # its context lives in this thread's slot
+        except BaseException as e:  # reported by the constructor
+            self._init_errors.append(e)
+        self._ready.wait()
+        if self._backends[slot] is None:
+            return
+        try:
+            while True:
+                with self._cv:
+                    while not self._queue and not self._closed:
+                        self._cv.wait()
+                    if not self._queue:
+                        break
+                    req, fut, t0 = self._queue.popleft()
+                    self._busy += 1
+                try:
+                    if fut.set_running_or_notify_cancel():
+                        with self._slot_locks[slot]:
+                            handle = self._admit(slot, req)
+                            out = self._backends[slot].run(handle, req)
+                        out["slot"] = slot
+                        with self._cv:
+                            self._lat.append(time.perf_counter() - t0)
+                        fut.set_result(out)
+                except BaseException as e:
+                    if not fut.done():
+                        fut.set_exception(e)
+                finally:
+                    with self._cv:
+                        self._busy -= 1
+                        self._cv.notify_all()
+        finally:
+            with self._slot_locks[slot]:
+                for h in self._caches[slot].values():
+                    self._backends[slot].release(h)
+                self._caches[slot].clear()
+            self._backends[slot].close()
+
+    def _count(self, name):
+        with self._cv:
+            self.counters[name] += 1
+
+    def _evict_one(self, slot):
+        """Release one least recently used operator: this slot's own first, then
+        an idle slot's.  False when nothing could be released."""
+        order = [slot] + [s for s in range(len(self._caches)) if s != slot]
+        for s in order:
+            lock = self._slot_locks[s]
+            if s != slot and not lock.acquire(blocking=False):
+                continue  # that slot is serving a request
+            try:
+                if self._caches[s]:
+                    _, h = self._caches[s].popitem(last=False)
+                    self._backends[s].release(h)
+                    self._count("evicted")
+                    return True
+            finally:
+                if s != slot:
+                    lock.release()
+        return False
+
+    def _admit(self, slot, req):
+        """The slot's operator for req: resident, or built once memory allows."""
+        key = req.key()
+        cache = self._caches[slot]
+        if key in cache:
+            cache.move_to_end(key)
+            self._count("reused")
+            return cache[key]
+        backend = self._backends[slot]
+        need = self._estimate_per_unknown() * req.ne
+        while True:
+            free, total = backend.memory()
+            if free - need >= self.reserve_fraction * total:
+                break
+            if self._evict_one(slot):
+                continue
+            with self._cv:
+                if self._busy <= 1:  # no other request in flight will free memory
+                    self.counters["rejected"] += 1
+                    raise MemoryError(f"operator for {req.ne} unknowns (~{need / 2**30:.1f} GiB) does not fit "
+                                      f"in the device-memory budget")
+                self._cv.wait(self.wait_s)
+        with self._build_lock:
+            free0 = backend.memory()[0]
+            handle = backend.build(req)
+            used = free0 - backend.memory()[0]
+        if used > 0:
+            with self._cv:
+                self._measured = max(self._measured, used / req.ne)
+        cache[key] = handle
+        self._count("built")
+        return handle

@@ -1,0 +1,107 @@
+"""Host logic of the request loop (paper_2003_11679_gb300/serve.py) with a fake
+backend: slots run requests at the same time, operators stay resident and
+are reused, least recently used ones are released when device memory runs
+short, and a request that can never fit is rejected.  No GPU is used.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2003_11679_gb300.serve import Request, Server
+
+
+class Device:
+    """One device's memory, shared by the fake backends of all slots."""
+
+    def __init__(self, total):
+        self.total, self.used, self.lock = total, 0, threading.Lock()
+
+
+class FakeBackend:
+    def __init__(self, dev, run_s=0.0):
+        self.dev, self.run_s = dev, run_s
+
+    def build(self, req):
+        with self.dev.lock:
+            self.dev.used += req.ne  # one byte per unknown
+        return {"size": req.ne, "key": req.key()}
+
+    def run(self, handle, req):
+        time.sleep(self.run_s)
+        return {"rcs": np.array([req.freq, req.sigma]), "iters": 1, "relres": 0.0}
+
+    def release(self, handle):
+        with self.dev.lock:
+            self.dev.used -= handle["size"]
+
+    def memory(self):
+        with self.dev.lock:
+            return self.dev.total - self.dev.used, self.dev.total
+
+    def close(self):
+        pass
+
+
+def _req(ne, freq=1e9, sigma=0.0):
+    V = np.zeros((3, 3))
+    T = np.zeros((2, 3), np.int32)
+    r = Request(V, T, freq, 1.0, sigma, [0, 0, -1], [1, 0, 0], [[0, 0, 1]])
+    r.ne = ne
+    return r
+
+
+def test_slots_overlap_and_latency_stats():
+    dev = Device(10 ** 9)
+    with Server(slots=2, backend_factory=lambda s: FakeBackend(dev, run_s=0.2), bytes_per_unknown=1) as srv:
+        t0 = time.perf_counter()
+        futs = [srv.submit(_req(10, freq=1e9 * (i + 1))) for i in range(4)]
+        outs = [f.result(timeout=30) for f in futs]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    assert wall < 0.75  # 4 requests of 0.2 s on 2 slots: two rounds, not four
+    assert [o["rcs"][0] for o in outs] == [1e9, 2e9, 3e9, 4e9]
+    assert {o["slot"] for o in outs} == {0, 1}
+    assert st["completed"] == 4 and st["p99_s"] >= st["p50_s"] > 0
+
+
+def test_resident_operator_is_reused():
+    dev = Device(10 ** 9)
+    with Server(slots=1, backend_factory=lambda s: FakeBackend(dev), bytes_per_unknown=1) as srv:
+        srv.submit(_req(100)).result(timeout=30)
+        srv.submit(_req(100)).result(timeout=30)
+        srv.submit(_req(100, sigma=1.0)).result(timeout=30)
+        st = srv.stats()
+    assert st["built"] == 2 and st["reused"] == 1
+    assert dev.used == 0  # close() released everything
+
+
+def test_least_recently_used_operator_is_released():
+    dev = Device(1000)  # reserve 10%: 900 usable
+    with Server(slots=1, backend_factory=lambda s: FakeBackend(dev), bytes_per_unknown=1) as srv:
+        srv.submit(_req(400, freq=1e9)).result(timeout=30)
+        srv.submit(_req(400, freq=2e9)).result(timeout=30)
+        srv.submit(_req(400, freq=1e9)).result(timeout=30)  # reuse: 1e9 becomes most recent
+        srv.submit(_req(400, freq=3e9)).result(timeout=30)  # needs room: releases 2e9
+        assert dev.used == 800
+        srv.submit(_req(400, freq=1e9)).result(timeout=30)  # still resident
+        st = srv.stats()
+    assert st["evicted"] == 1 and st["reused"] == 2 and st["built"] == 3
+
+
+def test_request_that_cannot_fit_is_rejected():
+    dev = Device(1000)
+    with Server(slots=2, backend_factory=lambda s: FakeBackend(dev), bytes_per_unknown=1) as srv:
+        with pytest.raises(MemoryError):
+            srv.submit(_req(950)).result(timeout=30)
+        assert srv.submit(_req(100)).result(timeout=30)["iters"] == 1
+        st = srv.stats()
+    assert st["rejected"] == 1
+
+
+def test_backend_failure_is_reported():
+    def factory(slot):
+        raise RuntimeError("no device")
+    with pytest.raises(RuntimeError, match="no device"):
+        Server(slots=2, backend_factory=factory)
