@@ -66,7 +66,8 @@ typedef struct sie_mesh sie_mesh;
 typedef struct sie_op sie_op;
 
 enum { SIE_FP64 = 0, SIE_MIXED = 1 };          /* grid-path precision */
-enum { SIE_DEVICE_PTRS = 1 };                  /* flags: vector args are device pointers */
+enum { SIE_DEVICE_PTRS = 1,                    /* flags: vector args are device pointers */
+       SIE_SOLVE_REFINE = 2 };                  /* sie_solve: mixed-precision iterative refinement */
 
 /* Which operator sie_matvec applies. */
 enum {
@@ -209,9 +210,18 @@ sie_status sie_op_near_csr(const sie_op* op, int which, int64_t* row_ptr, int32_
  * khat, epol: nrhs x 3 doubles (host).  b: complex128 nrhs x N_e. */
 sie_status sie_rhs_planewave(sie_op* op, const double* khat, const double* epol, int nrhs, double* b, int flags);
 
-/* Solve SYS x = b by restarted GMRES (FP64 Arnoldi).  x: complex128 N_e x
- * nrhs, H coefficients (n x H tested with RWG).  iters / relres: per rhs
- * (host arrays of nrhs, may be NULL). */
+/* Solve SYS x = b (Eq. sys) by restarted FGMRES (FP64 Arnoldi, right
+ * preconditioned by the AEFIE constraint preconditioner, zero initial guess)
+ * until the true relative residual is below tol_outer.  b, x: complex128,
+ * N_e + N_t per right-hand side ([H; c0 rho]), nrhs consecutive vectors.
+ * iters / relres: per rhs (host arrays of nrhs, may be NULL).
+ * flags: SIE_DEVICE_PTRS; SIE_SOLVE_REFINE = mixed-precision iterative
+ * refinement: the residual b - A x and the update use the FP64 product, each
+ * correction A d = r is solved with the complex64 product (as SIE_MIXED) to
+ * the accuracy the sweep needs, and the sweeps stop when the FP64 residual is
+ * below tol_outer (iters then counts the FGMRES iterations of all
+ * corrections).  Returns SIE_ERR_NOT_CONVERGED with the last iterate in x when
+ * maxit is reached first. */
 sie_status sie_solve(sie_op* op, const double* b, double* x, int nrhs, int* iters, double* relres, int flags);
 
 /* Monostatic/bistatic RCS (m^2) of the solution x (as returned by sie_solve,

@@ -21,6 +21,7 @@ SIE_OK = 0
 SIE_ERR_NOT_CONVERGED = 5
 SIE_FP64, SIE_MIXED = 0, 1
 SIE_DEVICE_PTRS = 1
+SIE_SOLVE_REFINE = 2
 SIE_RCS_STATIC_MAX_DIR = 2048
 SIE_OP_L0, SIE_OP_K0, SIE_OP_LI, SIE_OP_KI, SIE_OP_SYS, SIE_OP_ZI = range(6)
 
@@ -235,15 +236,17 @@ class Operator:
                                        SIE_DEVICE_PTRS if dev else 0))
         return b
 
-    def solve(self, b, x=None, nrhs=1, check=True):
-        """x = SYS^-1 b by FGMRES; returns (x, iters, relres)."""
+    def solve(self, b, x=None, nrhs=1, check=True, refine=False):
+        """x = SYS^-1 b by FGMRES; returns (x, iters, relres).  refine=True: mixed-
+        precision iterative refinement (complex64 corrections, FP64 residuals)."""
         if x is None:
             x = np.zeros_like(b)
         pb, db = _ptr(b)
         px, dx = _ptr(x)
         it = np.zeros(nrhs, np.int32)
         rr = np.zeros(nrhs)
-        code = lib().sie_solve(self.h, pb, px, nrhs, it.ctypes.data, rr.ctypes.data, SIE_DEVICE_PTRS if db else 0)
+        flags = (SIE_DEVICE_PTRS if db else 0) | (SIE_SOLVE_REFINE if refine else 0)
+        code = lib().sie_solve(self.h, pb, px, nrhs, it.ctypes.data, rr.ctypes.data, flags)
         if check or code != SIE_ERR_NOT_CONVERGED:
             _check(code)
         return x, it, rr

@@ -1238,7 +1238,8 @@ sie_status sie_solve(sie_op* op, const double* b, double* x, int nrhs, int* iter
         }
         int it = 0;
         double rr = 0;
-        sie_status s = sys_solve(op, br, xr, &it, &rr);
+        sie_status s = (flags & SIE_SOLVE_REFINE) ? sys_solve_refined(op, br, xr, &it, &rr)
+                                                  : sys_solve(op, br, xr, &it, &rr);
         if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
         if (s == SIE_ERR_NOT_CONVERGED) worst = s;
         if (iters) iters[r] = it;

@@ -241,6 +241,7 @@ struct sie_op {
     double2* g_io = nullptr;        // graph input x and output y, 2 (ne + nt)
     double* gstat = nullptr;        // device: max nested iterations and residual of graph runs
     size_t gnodes[2] = {0, 0};      // nodes of the last captured graph: outside the loop, loop body
+    double2* ir_buf = nullptr;      // iterative refinement: residual, correction, product (3 (ne + nt))
 };
 
 // ------------------------------------------------------------------ launchers (aim.cu, near.cu)
@@ -256,6 +257,7 @@ sie_status sys_prepare(sie_op* op);
 void sys_release(sie_op* op);
 sie_status sys_matvec(sie_op* op, int which, const double2* x, double2* y);
 sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres);
+sie_status sys_solve_refined(sie_op* op, const double2* b, double2* x, int* iters, double* relres);
 sie_status sys_rhs(sie_op* op, const double* khat, const double* epol, double2* b);
 // y = A x for an edge CSR matrix (overwrites y)
 sie_status csr_mv(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp, const int32_t* col,
