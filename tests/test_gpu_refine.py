@@ -2,7 +2,9 @@
 corrections run on the complex64 product, the residuals on the FP64 one, so
 the result meets the FP64 criterion (true relative residual below tol_outer)
 and its RCS equals the plain FP64 solve's up to that tolerance amplified by
-the conditioning (1e-4 relative is asked), and stays within 1% of Mie.
+the conditioning (1e-3 relative is asked), and stays within 1% of Mie.  The
+system product holds the nested interior solve, so its own accuracy is
+tol_inner: tol_inner = 1e-9 keeps it well below tol_outer = 1e-5.
 """
 import numpy as np
 import pytest
@@ -18,17 +20,17 @@ pytestmark = pytest.mark.gpu
 def test_refinement_meets_the_fp64_tolerance(lib, ctx, radius, f, eps_r, sigma):
     V, T = icosphere(2, radius, equal_volume=True)
     mesh = lib.Mesh(ctx, V, T)
-    op = lib.Operator(mesh, f, eps_r, 1.0, sigma, lib.params(tol_outer=1e-8))
+    op = lib.Operator(mesh, f, eps_r, 1.0, sigma, lib.params(tol_outer=1e-5, tol_inner=1e-9))
     try:
         b = op.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
         x64, it64, rr64 = op.solve(b)
         xr, itr, rrr = op.solve(b, refine=True)
-        assert rrr[0] < 1e-8 and rr64[0] < 1e-8
+        assert rrr[0] < 1e-5 and rr64[0] < 1e-5
         th = np.linspace(0.3, np.pi, 9)
         dirs = np.stack([np.sin(th), 0 * th, -np.cos(th)], 1)
         r64, rr = op.rcs(x64, dirs), op.rcs(xr, dirs)
         print("iters fp64", it64[0], "refined", itr[0], "rcs diff", np.abs(rr / r64 - 1).max())
-        assert np.abs(rr - r64).max() <= 1e-4 * np.abs(r64).max()
+        assert np.abs(rr - r64).max() <= 1e-3 * np.abs(r64).max()
         ref = mie.bistatic_rcs(th, 0.0, radius, f, eps_r, sigma)
         assert np.abs(rr / ref - 1).max() < 0.01
     finally:
