@@ -167,7 +167,10 @@ sie_status sie_op_set_solver(sie_op* op, const sie_params* params);
 /* Statistics of the last sie_solve on this operator (6 doubles): outer
  * iterations, outer relative residual, the largest nested (interior)
  * iteration count and residual, the largest constraint-preconditioner
- * iteration count and residual. */
+ * iteration count and residual.  A SIE_OP_SYS / SIE_OP_ZI sie_matvec clears
+ * the nested entries first, so after it they describe that call's nested
+ * solves (the way to check them for device-pointer calls, which do not
+ * synchronise).  Synchronises the context's stream. */
 sie_status sie_op_stats(const sie_op* op, double out[6]);
 
 /* Operator facts.  info (16 doubles): [0..2] grid N_x, N_y, N_z; [3..5] FFT
@@ -185,16 +188,22 @@ sie_status sie_op_info(const sie_op* op, double info[20]);
 /* grid origin (3) and spacing of the exterior grid */
 sie_status sie_op_grid(const sie_op* op, double origin[3], double* h, int64_t N[3]);
 
-/* y = A x for nrhs right-hand sides, A selected by `which` (SIE_OP_*).
+/* y = A x for nrhs right-hand sides, A selected by `which` (SIE_OP_*):
+ * Eqs. (AIM_Lin), (AIM_Kin) for L0/K0/LI/KI, Eq. (sys) for SYS, and Z_i of
+ * Eqs. (GIBCdef), (nest02), (nest2) for ZI.
  * x, y: complex128, length N_e (L0, K0, LI, KI, ZI) or N_e + N_t (SYS, the
  * AEFIE unknowns [H; c0 rho] of Eq. sys).  flags: SIE_DEVICE_PTRS or 0.
+ * SYS and ZI contain the nested solve of Eq. (nest2): one unrestarted FGMRES
+ * cycle of at most min(inner_maxit, 128) iterations to tol_inner.  When it
+ * ends above tol_inner, host-pointer calls return SIE_ERR_NOT_CONVERGED (y
+ * holds the product with that inexact Z_i); device-pointer calls do not
+ * synchronise and report it through sie_op_stats.
  * When the interior operator is near-region only and profiling is off, the
- * SYS product (nested solve of Eq. nest2 included) is captured on first use
- * into a CUDA graph, one per precision, and replayed; the nested iterations
- * are then a loop the device ends itself (at most min(restart, 60) and
- * inner_maxit iterations, no restart).  The environment variable SIE_GRAPH=0
- * selects the stream path.  The graph is dropped when tol_inner, inner_maxit
- * or restart change (sie_op_set_solver). */
+ * SYS product (nested solve included) is captured on first use into a CUDA
+ * graph, one per precision, and replayed; the nested iterations are then a
+ * loop the device ends itself, with the same iteration limit as the stream
+ * path.  The environment variable SIE_GRAPH=0 selects the stream path.  The
+ * graph is dropped when tol_inner or inner_maxit change (sie_op_set_solver). */
 sie_status sie_matvec(sie_op* op, int which, const double* x, double* y, int nrhs, int flags);
 
 /* Export the precorrected near-region matrix of an operator
@@ -221,13 +230,18 @@ sie_status sie_rhs_planewave(sie_op* op, const double* khat, const double* epol,
  * the accuracy the sweep needs, and the sweeps stop when the FP64 residual is
  * below tol_outer (iters then counts the FGMRES iterations of all
  * corrections).  Returns SIE_ERR_NOT_CONVERGED with the last iterate in x when
- * maxit is reached first. */
+ * maxit is reached first, or when a nested interior solve of its products
+ * ended above tol_inner (sie_op_stats gives both residuals). */
 sie_status sie_solve(sie_op* op, const double* b, double* x, int nrhs, int* iters, double* relres, int flags);
 
 /* Monostatic/bistatic RCS (m^2) of the solution x (as returned by sie_solve,
- * for the plane wave with polarisation epol, 1 V/m): for each observation
- * direction rhat (ndir x 3, host) the far-field cross section
- * 4 pi |E_s|^2 r^2.  rcs: ndir doubles (host).  One right-hand side. */
+ * for the plane wave with polarisation epol, 1 V/m), the quantity compared
+ * with the Mie series in Sec. V-A: for each observation direction rhat
+ * (ndir x 3, host) the far-field cross section 4 pi |E_s|^2 r^2 of the
+ * equivalent currents J = n x H and M = -n x E (E = Z_i H through the nested
+ * solve).  rcs: ndir doubles (host).  One right-hand side.  Returns
+ * SIE_ERR_NOT_CONVERGED (rcs filled) when that nested solve ended above
+ * tol_inner. */
 sie_status sie_rcs(sie_op* op, const double* x, const double* rhat, int ndir, double* rcs, int flags);
 
 /* Directions per sie_rcs_static call (bounds its static device array). */
@@ -252,6 +266,10 @@ sie_status sie_rcs(sie_op* op, const double* x, const double* rhat, int ndir, do
  * Set-up: the first call on each device looks up the array's address with
  * cudaGetSymbolAddress, that device current, and caches it; make that first
  * call before any stream capture begins on the device.
+ * What "allocates nothing" covers: no device memory is allocated or freed
+ * (no cudaMalloc, cudaMallocAsync, cudaFree or allocating library routine),
+ * and a successful call makes no host heap allocation either (only error
+ * messages allocate).
  * Sharing: all calls on one device use the same array, so calls that overlap
  * in time on a device (from other threads, streams or contexts) race on it;
  * the caller serialises them.  Each call returns once its results are on the

@@ -148,7 +148,8 @@ def green_lag(k, h, lag):
         g = -(1 + 1j * k * R) * e / (4 * np.pi * R ** 3)
     z = R == 0
     G = np.where(z, 0.0, G)
-    gv = np.where(z[..., None], 0.0, g[..., None] * d)
+    with np.errstate(invalid="ignore"):  # lag 0: g is inf there and is replaced by 0
+        gv = np.where(z[..., None], 0.0, g[..., None] * d)
     return G, gv
 
 

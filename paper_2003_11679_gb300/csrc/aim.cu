@@ -1151,6 +1151,7 @@ sie_status sie_matvec(sie_op* op, int which, const double* x, double* y, int nrh
     const int64_t ne = op->mesh->h.ne, nt = op->mesh->h.nt;
     const int64_t len = which == SIE_OP_SYS ? ne + nt : ne;
     bool dev = flags & SIE_DEVICE_PTRS;
+    if (which >= SIE_OP_SYS) SIE_TRY(nested_clear(op));
     for (int r = 0; r < nrhs; r++) {
         const double2* xr;
         double2* yr;
@@ -1173,7 +1174,11 @@ sie_status sie_matvec(sie_op* op, int which, const double* x, double* y, int nrh
         if (!dev)
             SIE_CUDA_TRY(cudaMemcpyAsync((double2*)y + r * len, yr, sizeof(double2) * len, cudaMemcpyDeviceToHost, st));
     }
-    if (!dev) SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!dev) {
+        SIE_CUDA_TRY(cudaStreamSynchronize(st));
+        // host buffers: the call synchronises anyway, so an inexact nested solve is reported here
+        if (which >= SIE_OP_SYS) return nested_check(op, "sie_matvec");
+    }
     return SIE_OK;
 }
 

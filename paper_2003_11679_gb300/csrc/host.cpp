@@ -21,6 +21,11 @@ sie_status build_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t
         set_error("sie_mesh_create: need at least 3 vertices and 4 triangles");
         return SIE_ERR_ARG;
     }
+    for (int64_t i = 0; i < 3 * nv; i++)
+        if (!std::isfinite(xyz[i])) {
+            set_error("sie_mesh_create: vertex coordinate " + std::to_string(i) + " is not finite");
+            return SIE_ERR_ARG;
+        }
     m.nv = nv;
     m.nt = nt;
     m.V.assign(xyz, xyz + 3 * nv);
@@ -564,7 +569,7 @@ sie_status sie_op_set_solver(sie_op* op, const sie_params* p)
         return SIE_ERR_ARG;
     }
     // the captured system-product graph bakes in the nested-solve settings
-    if (p->tol_inner != op->p.tol_inner || p->inner_maxit != op->p.inner_maxit || p->restart != op->p.restart)
+    if (p->tol_inner != op->p.tol_inner || p->inner_maxit != op->p.inner_maxit)
         sie::sys_graph_reset(op);
     op->p.tol_outer = p->tol_outer;
     op->p.tol_inner = p->tol_inner;

@@ -268,7 +268,12 @@ bool sys_z_workspace_ready(const sie_op* op);
 void sys_graph_reset(sie_op* op);
 // fold the nested-solve statistics of graph runs into op->stats (synchronises)
 void sys_stats_fold(sie_op* op);
-sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int ndir, double2* sums);
+sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int ndir, double2* sums,
+                        double* nested_res);
+// nested-solve statistics: clear them, or fold the graph's copy and return
+// SIE_ERR_NOT_CONVERGED when a nested solve ended above tol_inner
+sie_status nested_clear(sie_op* op);
+sie_status nested_check(sie_op* op, const char* who);
 double sys_rcs_scale(const sie_op* op);
 // nbatch consecutive grids (buf + k n^3, src + k N^3) in one launch per pass
 sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune,

@@ -133,8 +133,40 @@ __device__ cd ein(cd z)
     return cdivc(cexpc(mk(-z.re, -z.im)), f) + clogc(z) + mk(euler, 0);
 }
 
+// Numeric radial integrals over [0, rc] at height d.  Beyond R = RCUT/|Im k|
+// every direction whose edge lies farther away integrates the same truncated
+// range [0, rc(d)], so one evaluation serves all those directions of an
+// observation point (same sums, computed once).
+struct RadCache {
+    bool valid;
+    double rc;
+    cd a1, a2;
+};
+
+__device__ void radial_numeric(cd k, double rc, double d, cd* a1o, cd* a2o)
+{
+    cd a1 = mk(0, 0), a2 = mk(0, 0);
+    double hi = rc;
+    for (int p = 0; p < cq.npan && rc > 0.0; p++) {
+        double lo = (p == cq.npan - 1) ? 0.0 : hi * cq.ratio;
+        for (int qq = 0; qq < cq.n[QR_RAD]; qq++) {
+            double rho = lo + (hi - lo) * cq.x[QR_RAD][qq];
+            double wr = (hi - lo) * cq.w[QR_RAD][qq];
+            double R = sqrt(rho * rho + d * d);
+            cd z = mk(-k.im * R, k.re * R);  // j k R
+            cd e = cexpc(mk(-z.re, -z.im));
+            cd hz = cabsc(z) < 0.2 ? hfun(z) : (mk(1, 0) + z) * e - mk(1, 0);
+            a1 = a1 + (wr * rho * rho / R) * e;
+            a2 = a2 + (wr * rho * rho / (R * R * R)) * hz;
+        }
+        hi = lo;
+    }
+    *a1o = a1;
+    *a2o = a2;
+}
+
 // bounded radial remainders (series when |k| Rmax <= 1, else graded Gauss)
-__device__ void radial(cd k, double rhom, double d, double Rmax, cd* f1, cd* f2)
+__device__ void radial(cd k, double rhom, double d, double Rmax, cd* f1, cd* f2, RadCache* cache)
 {
     if (cabsc(k) * Rmax <= 1.0) {
         double rs = rhom / Rmax, ds = d / Rmax, Rs = sqrt(rs * rs + ds * ds), d2 = ds * ds;
@@ -182,30 +214,29 @@ __device__ void radial(cd k, double rhom, double d, double Rmax, cd* f1, cd* f2)
     // beyond R = RCUT/|Im k| the exponential is below 1e-15: f1 has no
     // contribution there and (1 + jkR) exp(-jkR) - 1 = -1 integrates in closed form
     double rc = rhom, tail = 0.0;
+    bool trunc = false;
     double kim = fabs(k.im);
     if (kim > 0.0) {
         double Rc = RCUT / kim, Rm = sqrt(rhom * rhom + d * d);
         if (Rc < Rm) {
+            trunc = true;
             rc = Rc > fabs(d) ? sqrt(Rc * Rc - d * d) : 0.0;
             double Rcc = sqrt(rc * rc + d * d);
             tail = (log(rhom + Rm) - rhom / Rm) - (log(rc + Rcc) - rc / Rcc);
         }
     }
-    cd a1 = mk(0, 0), a2 = mk(0, 0);
-    double hi = rc;
-    for (int p = 0; p < cq.npan && rc > 0.0; p++) {
-        double lo = (p == cq.npan - 1) ? 0.0 : hi * cq.ratio;
-        for (int qq = 0; qq < cq.n[QR_RAD]; qq++) {
-            double rho = lo + (hi - lo) * cq.x[QR_RAD][qq];
-            double wr = (hi - lo) * cq.w[QR_RAD][qq];
-            double R = sqrt(rho * rho + d * d);
-            cd z = mk(-k.im * R, k.re * R);  // j k R
-            cd e = cexpc(mk(-z.re, -z.im));
-            cd hz = cabsc(z) < 0.2 ? hfun(z) : (mk(1, 0) + z) * e - mk(1, 0);
-            a1 = a1 + (wr * rho * rho / R) * e;
-            a2 = a2 + (wr * rho * rho / (R * R * R)) * hz;
+    cd a1, a2;
+    if (trunc) {
+        // truncated: the range [0, rc] depends on d only
+        if (!cache->valid || cache->rc != rc) {
+            radial_numeric(k, rc, d, &cache->a1, &cache->a2);
+            cache->rc = rc;
+            cache->valid = true;
         }
-        hi = lo;
+        a1 = cache->a1;
+        a2 = cache->a2;
+    } else {
+        radial_numeric(k, rc, d, &a1, &a2);
     }
     a2 = a2 - mk(tail, 0);
     *f1 = a1;
@@ -230,6 +261,8 @@ __device__ void inner_polar(v3 r, v3 v0, v3 v1, v3 v2, cd k, Inner& o)
         if (nrm(r - c) - rc > RCUT / fabs(k.im)) return;
     }
     cd Is = mk(0, 0), Ign = mk(0, 0), Iv[3] = {mk(0, 0), mk(0, 0), mk(0, 0)}, Igt[3] = {mk(0, 0), mk(0, 0), mk(0, 0)};
+    RadCache rcache;
+    rcache.valid = false;
     double Omega = 0.0;
     cd mjk = mk(k.im, -k.re);  // -j k
     for (int i = 0; i < 3; i++) {
@@ -261,7 +294,7 @@ __device__ void inner_polar(v3 r, v3 v0, v3 v1, v3 v2, cd k, Inner& o)
             double Rm = sqrt(rhom * rhom + dd * dd);
             cd is = cexpc(mjk * ad) * (Rm - ad) * phi1(mjk * (Rm - ad));
             cd f1, f2;
-            radial(k, rhom, dd, Rmax, &f1, &f2);
+            radial(k, rhom, dd, Rmax, &f1, &f2, &rcache);
             cd igt = mk(log(rhom + Rm) - rhom / Rm, 0) + f2;
             cd ign = (-dd / Rm) * cexpc(mjk * Rm);
             Is = Is + wa * is;

@@ -110,11 +110,16 @@ sie_status sie_rcs_static(sie_op* op, const double* x, const double* rhat, int n
     }
     SIE_CUDA_TRY(cudaMemcpyAsync(s + OFF_RHAT, rhat, sizeof(double) * 3 * ndir, cudaMemcpyHostToDevice, st));
     double2* sums = reinterpret_cast<double2*>(s + OFF_SUMS);
-    SIE_TRY(sys_far_sums(op, xr, s + OFF_RHAT, ndir, sums));
+    double nres = 0.0;
+    SIE_TRY(sys_far_sums(op, xr, s + OFF_RHAT, ndir, sums, &nres));
     k_rcs_sigma<<<(ndir + 127) / 128, 128, 0, st>>>(ndir, sys_rcs_scale(op), s + OFF_RHAT, sums, s + OFF_RCS);
     SIE_CUDA_TRY(cudaGetLastError());
     SIE_CUDA_TRY(cudaMemcpyAsync(rcs, s + OFF_RCS, sizeof(double) * ndir, cudaMemcpyDeviceToHost, st));
     SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (nres >= op->p.tol_inner) {
+        set_error("sie_rcs_static: the nested interior solve of Z_i H ended above tol_inner");
+        return SIE_ERR_NOT_CONVERGED;
+    }
     return SIE_OK;
 }
 

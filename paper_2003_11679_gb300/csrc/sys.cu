@@ -9,7 +9,6 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
-#include <functional>
 #include <vector>
 
 #include "internal.h"
@@ -135,7 +134,20 @@ static sie_status axpby(cudaStream_t st, int64_t n, cplx a, const double2* x, cp
 }
 
 // ------------------------------------------------------------------ FGMRES
-using Apply = std::function<sie_status(const double2*, double2*)>;
+// Non-owning reference to an operator y = A x (a lambda that outlives the
+// call it is passed to): unlike std::function it never allocates.
+class Apply {
+    const void* obj_ = nullptr;
+    sie_status (*call_)(const void*, const double2*, double2*) = nullptr;
+
+public:
+    template <class F>
+    Apply(const F& f)  // NOLINT: implicit from a named callable
+        : obj_(&f), call_([](const void* o, const double2* x, double2* y) { return (*static_cast<const F*>(o))(x, y); })
+    {
+    }
+    sie_status operator()(const double2* x, double2* y) const { return call_(obj_, x, y); }
+};
 
 sie_status KrylovWork::alloc(cudaStream_t st, int64_t n_, int m_)
 {
@@ -527,6 +539,10 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
             it++;
             if (j >= LAG) {
                 SIE_CUDA_TRY(cudaEventSynchronize(K.ev[j - LAG]));
+                if (!std::isfinite(K.resid_h[j - LAG])) {
+                    set_error("GMRES: the residual is not finite (non-finite right-hand side or operator)");
+                    return SIE_ERR_ARG;
+                }
                 if (K.resid_h[j - LAG] < tol) {
                     conv = true;
                     j++;
@@ -537,6 +553,10 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
         const int jend = j - 1;
         SIE_CUDA_TRY(cudaEventSynchronize(K.ev[jend]));
         rel = K.resid_h[jend];
+        if (!std::isfinite(rel)) {
+            set_error("GMRES: the residual is not finite (non-finite right-hand side or operator)");
+            return SIE_ERR_ARG;
+        }
         if (rel < tol) conv = true;
         k_gm_backsub<<<1, 1, 0, st>>>(jend, m, H, g, y);
         k_gemv<<<nb(n), 256, 0, st>>>(n, jend + 1, K.Z, n, y, 1.0, x);
@@ -1125,8 +1145,14 @@ static GL8 gl_rule(int n)
 static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork& K, double tol, const double2* v,
                                    double2* y);
 
+// Krylov basis of the nested solve: it runs without restart, so the graph's
+// device-ended loop and the stream path take the same iterations
+constexpr int INNER_BASIS_MAX = 128;
+static int inner_m(const sie_op* op) { return std::max(1, std::min(op->p.inner_maxit, INNER_BASIS_MAX)); }
+
 // interior impedance E' = Z' H = -(j k0 eps_r + sigma eta0)^-1 L_i^-1 (K_i - Ix/2) H
-static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_iters)
+// nested_res (stream path): relative residual the nested solve ended with
+static sie_status apply_Z(sie_op* op, const double2* H, double2* E, double* nested_res)
 {
     sie_ctx* c = op->mesh->ctx;
     cudaStream_t st = c->stream;
@@ -1135,39 +1161,38 @@ static sie_status apply_Z(sie_op* op, const double2* H, double2* E, int* inner_i
     SIE_TRY(aim_apply(op, op->inn, 1, H, a));
     SIE_TRY(spmv(st, (int)ne, op->ix_nnz, op->ix_row_ptr, op->ix_col, op->ix_val, H, cplx(-0.5, 0), a));
     AimOp& I = op->inn;
-    Apply A = [&](const double2* x, double2* y) { return aim_apply(op, I, 0, x, y); };
+    auto A = [&](const double2* x, double2* y) { return aim_apply(op, I, 0, x, y); };
     cplx ki(I.kr, I.ki);
     // Nested preconditioner M_i of Eq. (nest2pc) in its near-region form: the
     // constraint form (diag LA_i + near Lphi_i, block elimination) when the
     // object has an interior grid, and when it is near-region only (skin depth
     // below the near region, L_i = L_i,NR) a sparse approximate inverse of
     // L_i,NR on its own pattern, applied as one CSR product
-    Apply Minv;
-    if (I.has_grid) {
-        Minv = [&](const double2* x, double2* y) {
-            return constraint_solve(op, I, 1.0 / (ki * ki), op->kcs_in, op->p.tol_constraint_inner, x, y);
-        };
-    } else {
-        Minv = [&](const double2* x, double2* y) {
-            Stage s_(c, "spai_apply");
-            return csr_mv(c->stream, (int)ne, I.nnz, I.row_ptr, I.col, I.valM, x, y);
-        };
-    }
-    const int m_in = std::min(op->p.restart, 60);
+    auto Mconstraint = [&](const double2* x, double2* y) {
+        return constraint_solve(op, I, 1.0 / (ki * ki), op->kcs_in, op->p.tol_constraint_inner, x, y);
+    };
+    auto Mspai = [&](const double2* x, double2* y) {
+        Stage s_(c, "spai_apply");
+        return csr_mv(c->stream, (int)ne, I.nnz, I.row_ptr, I.col, I.valM, x, y);
+    };
+    const Apply Minv = I.has_grid ? Apply(Mconstraint) : Apply(Mspai);
+    // one unrestarted cycle of at most min(inner_maxit, INNER_BASIS_MAX) iterations
+    const int m_in = inner_m(op);
+    if (nested_res) *nested_res = 0.0;
     if (op->capturing && !I.has_grid) {
         // inside the system-product graph: device-controlled nested cycle
-        SIE_TRY(fgmres_dev(c, op->gs[1], op->kin, ne, A, Minv, a, E, op->p.tol_inner, op->p.inner_maxit, m_in,
-                           op->gstat, &op->gnodes[1]));
+        SIE_TRY(fgmres_dev(c, op->gs[1], op->kin, ne, A, Minv, a, E, op->p.tol_inner, m_in, m_in, op->gstat,
+                           &op->gnodes[1]));
     } else {
         int it = 0;
         double rr = 0;
         sie_status s;
         {
             Stage s_(c, "inner_solve");
-            s = fgmres(c, op->kin, ne, A, Minv, a, E, op->p.tol_inner, op->p.inner_maxit, m_in, &it, &rr);
+            s = fgmres(c, op->kin, ne, A, Minv, a, E, op->p.tol_inner, m_in, m_in, &it, &rr);
         }
         if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
-        if (inner_iters) *inner_iters = it;
+        if (nested_res) *nested_res = rr;
         op->stats[2] = std::max(op->stats[2], (double)it);
         op->stats[3] = std::max(op->stats[3], rr);
     }
@@ -1297,7 +1322,7 @@ static sie_status build_sys_graph(sie_op* op)
     sie_ctx* c = op->mesh->ctx;
     const int64_t ne = op->mesh->h.ne, n = ne + op->mesh->h.nt;
     // everything the product touches exists before the capture starts
-    SIE_TRY(op->kin.alloc(c->stream, ne, std::min(op->p.restart, 60)));
+    SIE_TRY(op->kin.alloc(c->stream, ne, inner_m(op)));
     if (!op->g_io) SIE_CUDA_TRY(cudaMallocAsync((void**)&op->g_io, sizeof(double2) * 2 * n, c->stream));
     if (!op->gstat) {
         SIE_CUDA_TRY(cudaMallocAsync((void**)&op->gstat, sizeof(double) * 2, c->stream));
@@ -1381,7 +1406,7 @@ static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork&
     k_jacobi<<<nb(ne), 256, 0, st>>>(ne, v, a.dLA, make_double2(1.0, 0.0), t1);
     k_D<<<nb(nt), 256, 0, st>>>((int)nt, M, t1, rq);
     SIE_CUDA_TRY(cudaGetLastError());
-    Apply S = [&](const double2* x, double2* out) {
+    auto S = [&](const double2* x, double2* out) {
         // out = x - kappa D Dg^-1 D^T Lphi x
         SIE_TRY(spmv(st, (int)nt, tri_nnz(a), a.tri_row_ptr, a.tri_col, a.valLphiNR, x, 1.0, ph, false));
         SIE_CUDA_TRY(cudaMemsetAsync(te, 0, sizeof(double2) * ne, st));
@@ -1391,7 +1416,7 @@ static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork&
         SIE_CUDA_TRY(cudaGetLastError());
         return axpby(st, nt, 1.0, x, -kappa, out);
     };
-    Apply I = [&](const double2* x, double2* out) {
+    auto I = [&](const double2* x, double2* out) {
         SIE_CUDA_TRY(cudaMemcpyAsync(out, x, sizeof(double2) * nt, cudaMemcpyDeviceToDevice, st));
         return SIE_OK;
     };
@@ -1540,11 +1565,33 @@ sie_status sys_matvec(sie_op* op, int which, const double2* x, double2* y)
     return apply_Z(op, x, y, nullptr);
 }
 
+// SIE_ERR_NOT_CONVERGED when a nested (interior) solve of the products since
+// the statistics were last cleared ended above tol_inner (synchronises)
+sie_status nested_check(sie_op* op, const char* who)
+{
+    sys_stats_fold(op);
+    if (op->stats[3] >= op->p.tol_inner) {
+        set_error(std::string(who) + ": a nested interior solve ended at relative residual " +
+                  std::to_string(op->stats[3]) + " >= tol_inner after min(inner_maxit, " +
+                  std::to_string(INNER_BASIS_MAX) + ") iterations; the result uses that inexact Z_i");
+        return SIE_ERR_NOT_CONVERGED;
+    }
+    return SIE_OK;
+}
+
+// clear the nested-solve statistics (host and graph copies)
+sie_status nested_clear(sie_op* op)
+{
+    op->stats[2] = op->stats[3] = 0;
+    if (op->gstat) SIE_CUDA_TRY(cudaMemsetAsync(op->gstat, 0, sizeof(double) * 2, op->mesh->ctx->stream));
+    return SIE_OK;
+}
+
 sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres)
 {
     const int64_t n = op->mesh->h.ne + op->mesh->h.nt;
-    Apply A = [&](const double2* u, double2* v) { return apply_sys_fast(op, u, v); };
-    Apply Minv = [&](const double2* u, double2* v) { return precond_sys(op, u, v); };
+    auto A = [&](const double2* u, double2* v) { return apply_sys_fast(op, u, v); };
+    auto Minv = [&](const double2* u, double2* v) { return precond_sys(op, u, v); };
     for (int i = 2; i < 6; i++) op->stats[i] = 0;
     if (op->gstat) SIE_CUDA_TRY(cudaMemsetAsync(op->gstat, 0, sizeof(double) * 2, op->mesh->ctx->stream));
     int it = 0;
@@ -1555,6 +1602,7 @@ sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, doubl
     op->stats[1] = rr;
     if (iters) *iters = it;
     if (relres) *relres = rr;
+    if (s == SIE_OK) s = nested_check(op, "sie_solve");
     return s;
 }
 
@@ -1591,8 +1639,8 @@ sie_status sys_solve_refined(sie_op* op, const double2* b, double2* x, int* iter
     double2* dot = op->kout.h;
     double* hbuf = op->kout.resid_h;
     const int saved = op->p.precision;
-    Apply A32 = [&](const double2* u, double2* v) { return apply_sys_fast(op, u, v); };
-    Apply Minv = [&](const double2* u, double2* v) { return precond_sys(op, u, v); };
+    auto A32 = [&](const double2* u, double2* v) { return apply_sys_fast(op, u, v); };
+    auto Minv = [&](const double2* u, double2* v) { return precond_sys(op, u, v); };
     for (int i = 2; i < 6; i++) op->stats[i] = 0;
     if (op->gstat) SIE_CUDA_TRY(cudaMemsetAsync(op->gstat, 0, sizeof(double) * 2, st));
     SIE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
@@ -1632,7 +1680,8 @@ sie_status sys_solve_refined(sie_op* op, const double2* b, double2* x, int* iter
     op->stats[1] = rel;
     if (iters) *iters = total;
     if (relres) *relres = rel;
-    return rel < op->p.tol_outer ? SIE_OK : SIE_ERR_NOT_CONVERGED;
+    if (!(rel < op->p.tol_outer)) return SIE_ERR_NOT_CONVERGED;
+    return nested_check(op, "sie_solve (refined)");
 }
 
 sie_status sys_rhs(sie_op* op, const double* khat, const double* epol, double2* b)
@@ -1651,7 +1700,8 @@ sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, d
     cudaStream_t st = op->mesh->ctx->stream;
     const DevMesh& M = op->mesh->d;
     double2* E = op->sys_E;
-    SIE_TRY(apply_Z(op, x, E, nullptr));
+    double nres = 0.0;
+    SIE_TRY(apply_Z(op, x, E, &nres));
     double *dr = nullptr;
     double2* dout = nullptr;
     SIE_CUDA_TRY(cudaMallocAsync((void**)&dr, sizeof(double) * 3 * ndir, st));
@@ -1679,6 +1729,11 @@ sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, d
         double s = std::norm(v[0]) + std::norm(v[1]) + std::norm(v[2]);
         rcs[d] = op->k0 * op->k0 * ETA0 * ETA0 / (4 * M_PI) * s;
     }
+    if (nres >= op->p.tol_inner) {
+        set_error("sie_rcs: the nested interior solve of Z_i H ended at relative residual " + std::to_string(nres) +
+                  " >= tol_inner");
+        return SIE_ERR_NOT_CONVERGED;
+    }
     return SIE_OK;
 }
 
@@ -1688,7 +1743,7 @@ sie_status sys_rcs(sie_op* op, const double2* x, const double* rhat, int ndir, d
 bool sys_z_workspace_ready(const sie_op* op)
 {
     const int64_t ne = op->mesh->h.ne, nt = op->mesh->h.nt;
-    if (op->kin.n != ne || op->kin.m != std::min(op->p.restart, 60)) return false;
+    if (op->kin.n != ne || op->kin.m != inner_m(op)) return false;
     if (op->inn.has_grid && (op->kcs_in.n != nt || op->kcs_in.m != op->p.constraint_restart)) return false;
     return true;
 }
@@ -1696,10 +1751,11 @@ bool sys_z_workspace_ready(const sie_op* op)
 // E' = Z' x[0:ne] into op->sys_E, then the far-field sums N(H), N(E') of the
 // directions rhat_d (device, 3 doubles each) into sums (device, 6 complex per
 // direction): the device half of sys_rcs, with caller-owned buffers.
-sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int ndir, double2* sums)
+sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int ndir, double2* sums,
+                        double* nested_res)
 {
     cudaStream_t st = op->mesh->ctx->stream;
-    SIE_TRY(apply_Z(op, x, op->sys_E, nullptr));
+    SIE_TRY(apply_Z(op, x, op->sys_E, nested_res));
     k_far<<<ndir, 256, 0, st>>>(op->mesh->d.nt, op->mesh->d, gl_rule(6), op->k0, rhat_d, x, op->sys_E, sums);
     SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;

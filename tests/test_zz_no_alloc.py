@@ -105,3 +105,49 @@ def test_profiling_on_is_refused(lib, ctx, solved):
     finally:
         ctx.profile(False)
     assert code == 7  # SIE_ERR_STATE
+
+
+def _pool_bytes():
+    """(used, reserved, used high-water mark) of device 0's default stream-ordered
+    memory pool, read through the driver API (the pool every cudaMallocAsync of
+    the library draws from), after the high-water mark is reset to the current
+    use."""
+    cu = ctypes.CDLL("libcuda.so.1")
+    dev = ctypes.c_int()
+    assert cu.cuDeviceGet(ctypes.byref(dev), 0) == 0
+    pool = ctypes.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    RESERVED_CURRENT, USED_CURRENT, USED_HIGH = 5, 7, 8
+
+    def get(attr):
+        v = ctypes.c_uint64()
+        assert cu.cuMemPoolGetAttribute(pool, attr, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high():
+        z = ctypes.c_uint64(0)
+        assert cu.cuMemPoolSetAttribute(pool, USED_HIGH, ctypes.byref(z)) == 0
+
+    return get, reset_high, (RESERVED_CURRENT, USED_CURRENT, USED_HIGH)
+
+
+def test_calls_allocate_no_device_memory(lib, solved):
+    """Repeated calls leave the device allocations as they were: the pool's
+    used and reserved bytes and its high-water mark do not move (a stream-ordered
+    allocation and free inside a call would raise the mark), and neither does
+    the device's free memory (plain cudaMalloc)."""
+    import torch
+    op, x = solved.op, solved.x
+    d = _dirs(64, 9)
+    op.rcs_static(x, d)  # first call on the device: symbol lookup done
+    torch.cuda.synchronize()
+    get, reset_high, (RES, USED, HIGH) = _pool_bytes()
+    reset_high()
+    used0, res0 = get(USED), get(RES)
+    free0 = torch.cuda.mem_get_info()[0]
+    for s in range(3):
+        op.rcs_static(x, _dirs(64 + s, 10 + s))
+    torch.cuda.synchronize()
+    assert get(HIGH) == used0
+    assert get(USED) == used0 and get(RES) == res0
+    assert torch.cuda.mem_get_info()[0] == free0
