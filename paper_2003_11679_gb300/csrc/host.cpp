@@ -98,7 +98,12 @@ sie_status build_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t
         n[1] = e1[2] * e2[0] - e1[0] * e2[2];
         n[2] = e1[0] * e2[1] - e1[1] * e2[0];
         double twoA = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-        if (!(twoA > 0)) {
+        double e3[3] = {c[0] - b[0], c[1] - b[1], c[2] - b[2]};
+        double lmax2 = std::max({e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2],
+                                 e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2],
+                                 e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]});
+        // collinear up to rounding: area below 1e-10 of the longest edge squared
+        if (!(twoA > 1e-10 * lmax2)) {
             set_error("sie_mesh_create: degenerate triangle");
             return SIE_ERR_MESH;
         }

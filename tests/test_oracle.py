@@ -325,3 +325,138 @@ def test_mie_identities():
     pec = mie.backscatter_rcs(1e-3, 10e9, pec=True)
     cu = mie.backscatter_rcs(1e-3, 10e9, 1.0, 5.8e7)
     assert abs(cu / pec - 1) < 2e-3
+
+
+# ------------------------------------------------------------------ touching pairs: independent rule
+# tests/touching_quadrature.py integrates the same 14 moments by relative
+# coordinates and Duffy cone maps (no polar inner integration, no graded outer
+# rule), so it shares no step with the oracle's near-field rule (mom.c).
+import sys  # noqa: E402
+
+sys.path.insert(0, os.path.dirname(__file__))
+import touching_quadrature as tq  # noqa: E402
+
+# the oracle's rule with every knob refined well past the defaults
+REFINED = dict(po=9, na=16, nr=16, opan=14, olam=10, omu=10, emu=8, emupan=4, npan=12, alen=0.75)
+
+
+def test_touching_rule_static_self_similarity():
+    """For the kernel 1/R (homogeneous of degree -1) the self term of a triangle
+    equals twice the sum of the touching child pairs of its midpoint subdivision
+    (the four self terms are each 1/8 of the parent's): ties the identical,
+    edge-adjacent and vertex-adjacent branches together; plus convergence in n."""
+    A, B, C = np.array([0, 0, 0.0]), np.array([1, 0, 0.0]), np.array([0.4, 0.8, 0.0])
+    V = np.array([A, B, C, (A + B) / 2, (B + C) / 2, (C + A) / 2])
+    T = np.array([(0, 3, 5), (3, 1, 4), (5, 4, 2), (4, 5, 3)])
+    k = 1e-14
+    parent = tq.self_moments(A, B, C, k, n=16)[0]
+    kids = sum(tq.touching_moments(V, T, i, j, k, n=16)[0] for i in range(4) for j in range(4) if i != j)
+    assert abs(2 * kids - parent) <= 1e-12 * abs(parent)
+    for s in range(1, 4):
+        a = tq.touching_moments(V, T, 0 if s != 3 else 3, s if s != 3 else 0, 5.0 - 5.0j, n=12)
+        b = tq.touching_moments(V, T, 0 if s != 3 else 3, s if s != 3 else 0, 5.0 - 5.0j, n=18)
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+
+
+def _touching_case(kl):
+    V, T = icosphere(2, 1.0)
+    m = Mesh(V, T)
+    t = 5
+    nb = [s for s in range(m.nt) if len(set(T[t]) & set(T[s])) > 0]
+    lbar = m.edge_len.mean()
+    k = (kl / np.sqrt(2)) * (1 - 1j) / lbar if kl > 1 else kl / lbar
+    ref = np.array([tq.touching_moments(V, T, t, s, k, n=14) for s in nb])
+    return m, t, nb, k, ref
+
+
+def _touching_errors(m, t, nb, k, ref, quad):
+    got = mom.pair_moments(m, np.array([[t, s] for s in nb]), k, quad)
+    eQ = max(np.abs(got[i, :8] - ref[i, :8]).max() / np.abs(ref[i, :8]).max() for i in range(len(nb)))
+    # self pair: U = V = 0 (antisymmetric integrands), compared on the other pairs
+    eK = max(np.abs(got[i, 8:] - ref[i, 8:]).max() / np.abs(ref[i, 8:]).max() for i, s in enumerate(nb) if s != t)
+    return eQ, eK
+
+
+# lighter refinement for the copper regime (more outer points per graded panel
+# and along the shared edge, more radial points): the dominant knobs there
+REFINED_LOSSY = dict(olam=10, emu=8, nr=12)
+
+
+@pytest.mark.parametrize("kl,quad,tol_ref,tol_def", [(0.2, REFINED, (1e-10, 5e-8), (2e-6, 3e-5)),
+                                                     (80.0, REFINED_LOSSY, (5e-6, 1e-4), (5e-3, 6e-3))],
+                         ids=["lossless", "copper"])
+def test_oracle_touching_moments_vs_independent_rule(kl, quad, tol_ref, tol_def):
+    """All 14 moments of the self, 3 edge-adjacent and 9 vertex-adjacent pairs of
+    one triangle: (a) the oracle's rule with refined knobs converges to the
+    independent relative-coordinate rule (a wrong sign, index or term in either
+    would not); (b) the error of the default knobs, |k| l = 0.2 (lossless) and
+    |k| l = 80 with Im k = -Re k (copper at 10 GHz on 38 um edges): Q moments
+    (L operators) and U, V (K operator)."""
+    m, t, nb, k, ref = _touching_case(kl)
+    eQ, eK = _touching_errors(m, t, nb, k, ref, quad)
+    assert eQ <= tol_ref[0] and eK <= tol_ref[1], (eQ, eK)
+    eQ, eK = _touching_errors(m, t, nb, k, ref, None)
+    print(f"default rule |k|l={kl}: Q {eQ:.2e} K {eK:.2e}")
+    assert eQ <= tol_def[0] and eK <= tol_def[1], (eQ, eK)
+
+
+# ------------------------------------------------------------------ Mie: plain definition at high precision
+def _mie_plain(x, m, nmax, dps=60):
+    """a_n, b_n from their definition with Riccati-Bessel functions
+    psi_n(z) = z j_n(z), xi_n(z) = z h_n^(1)(z) evaluated in mpmath (no
+    logarithmic-derivative recurrence)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = dps
+    x = mp.mpf(x)
+    m = mp.mpc(m.real, m.imag)
+    z = m * x
+
+    def jn(n, u):
+        return mp.sqrt(mp.pi / (2 * u)) * mp.besselj(n + mp.mpf(1) / 2, u)
+
+    def yn(n, u):
+        return mp.sqrt(mp.pi / (2 * u)) * mp.bessely(n + mp.mpf(1) / 2, u)
+
+    def psi(n, u):
+        return u * jn(n, u)
+
+    def dpsi(n, u):  # d/du [u j_n(u)] = u j_{n-1}(u) - n j_n(u)
+        return u * jn(n - 1, u) - n * jn(n, u)
+
+    def xi(n, u):
+        return u * (jn(n, u) + 1j * yn(n, u))
+
+    def dxi(n, u):
+        return u * (jn(n - 1, u) + 1j * yn(n - 1, u)) - n * (jn(n, u) + 1j * yn(n, u))
+
+    a, b = [], []
+    for n in range(1, nmax + 1):
+        pz, dpz, px, dpx, xx, dxx = psi(n, z), dpsi(n, z), psi(n, x), dpsi(n, x), xi(n, x), dxi(n, x)
+        a.append(complex((m * pz * dpx - px * dpz) / (m * pz * dxx - xx * dpz)))
+        b.append(complex((pz * dpx - m * px * dpz) / (pz * dxx - m * xx * dpz)))
+    return np.array(a), np.array(b)
+
+
+@pytest.mark.parametrize("x,eps_r,sigma_over_weps0", [(0.6283, 4.0, 0.0), (3.0, 2.25, 0.3), (0.2096, 1.0, 1.043e8)],
+                         ids=["dielectric", "lossy", "copper"])
+def test_mie_coefficients_vs_plain_definition(x, eps_r, sigma_over_weps0):
+    """The oracle's a_n, b_n (downward log-derivative recurrence, scipy Bessel
+    functions) equal the Bohren-Huffman definition evaluated at 60 digits,
+    including the copper case where |m x| is about 2e3."""
+    m = np.sqrt(eps_r + 1j * sigma_over_weps0 + 0j)
+    a, b = mie.coefficients(x, m)
+    pa, pb = _mie_plain(x, m, len(a))
+    assert np.abs(a - pa).max() <= 1e-11 * np.abs(pa).max()
+    assert np.abs(b - pb).max() <= 1e-11 * np.abs(pb).max()
+
+
+def test_mie_angular_functions_low_orders():
+    """S1, S2 with only a_1 or b_1 or a_2 or b_2 set: (3/2) pi_1 = 3/2,
+    (3/2) tau_1 = (3/2) cos t, (5/6) pi_2 = (5/2) cos t, (5/6) tau_2 = (5/2) cos 2t."""
+    th = np.linspace(0.0, np.pi, 7)
+    c = np.cos(th)
+    cases = [((1, 0), (0, 0), 1.5 * np.ones_like(th), 1.5 * c), ((0, 0), (1, 0), 1.5 * c, 1.5 * np.ones_like(th)),
+             ((0, 1), (0, 0), 2.5 * c, 2.5 * np.cos(2 * th)), ((0, 0), (0, 1), 2.5 * np.cos(2 * th), 2.5 * c)]
+    for a, b, s1, s2 in cases:
+        S1, S2 = mie.amplitudes(th, 1.0, np.array(a, complex), np.array(b, complex))
+        assert np.abs(S1 - s1).max() < 1e-14 and np.abs(S2 - s2).max() < 1e-14
