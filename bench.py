@@ -12,15 +12,24 @@ solve, seven source grids projected, 7 forward + 4 inverse pruned 3D FFTs,
 spectral multiply with G and grad G, interpolation, and the precorrected
 near-region products.  value = RWG unknowns x system matvecs / s, whole job.
 The JSON line also reports GMRES solves/s and p50/p99 solve latency of the
-dielectric-sphere workload (1,920 RWG), which converges with the default
-preconditioner.
+dielectric-sphere workload (1,920 RWG, equal-volume mesh), FP64 and with
+mixed-precision iterative refinement on the same right-hand sides, each solve's
+backscatter RCS checked against the Mie series (1%).
 
---impl reference times the CPU oracle (numpy FFT grid products) on the same
-workload and metric.
+The FP64 path's roofline fractions use the FP64 FMA throughput the library's
+probe kernel measures in the same run (sie_probe_fma).
+
+--impl reference (and the cpu_baseline object) time the oracle's system
+product of Eq. (sys) -- AIM exterior with its near terms, near-region-only
+interior Z' by a sparse LU -- on a bounded sample of the workload: the same
+sphere, material and exterior grid (the same 128^3 FFT convolutions) on a
+320-triangle mesh.  The grid part dominates its cost and has the full size, so
+N_e(full) / (step time) is an upper bound of the oracle's full-size throughput.
 """
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -40,15 +49,40 @@ def workload(name):
     from synth import icosphere
     if name == "lossy-sphere-30720":
         V, T = icosphere(5, 1e-3)
-        return dict(V=V, T=T, f=10e9, eps_r=1.0, sigma=5.8e7, grid_n=64,
+        return dict(V=V, T=T, f=10e9, eps_r=1.0, sigma=5.8e7, grid_n=64, radius=1e-3, level=5,
                     desc="copper sphere r=1mm, sigma=5.8e7 S/m, 10 GHz, 20480 triangles / 30720 RWG, "
-                         "grid 64^3 (FFT 128^3), complex128, near-only interior, 1 RHS")
+                         "grid 63^3 (grid_n 64, FFT 128^3), complex128, near-only interior, 1 RHS")
     if name == "dielectric-sphere-1920":
-        V, T = icosphere(3, 1e-2)
-        return dict(V=V, T=T, f=3e9, eps_r=4.0, sigma=0.0, grid_n=0,
-                    desc="dielectric sphere r=1cm, eps_r=4, 3 GHz, 1280 triangles / 1920 RWG, h=0.5 mean edge, "
-                         "complex128, AIM interior, 1 RHS")
+        V, T = icosphere(3, 1e-2, equal_volume=True)
+        return dict(V=V, T=T, f=3e9, eps_r=4.0, sigma=0.0, grid_n=0, radius=1e-2, level=3,
+                    desc="dielectric sphere r=1cm, eps_r=4, 3 GHz, 1280 triangles / 1920 RWG (equal-volume "
+                         "icosphere), h=0.5 mean edge, complex128, AIM interior, 1 RHS")
     raise SystemExit(f"unknown workload {name}")
+
+
+def mie_backscatter(name):
+    """The Mie-series backscatter RCS of a workload's sphere, as stored by
+    tests/golden/make_mie_backscatter.py (from the oracle's Mie series)."""
+    path = os.path.join(ROOT, "tests", "golden", "mie_backscatter.txt")
+    for line in open(path):
+        f = line.split()
+        if f and f[0] == name:
+            return float(f[5])
+    raise KeyError(name)
+
+
+def cpu_info():
+    """Host CPU model (lscpu, else platform) and logical core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return model or platform.processor() or platform.machine(), os.cpu_count()
 
 
 def dist_env():
@@ -157,7 +191,26 @@ def stage_model(stage, info, ne, nt, nnz_ext, nnz_int):
 # grids per FFT launch in the system product: 7 forward (H, E, rho sources), 4 inverse
 FFT_GRIDS = {"fft_fwd_x": 7, "fft_fwd_y": 7, "fft_fwd_z": 7, "fft_inv_z": 4, "fft_inv_y": 4, "fft_inv_x": 4}
 
-FP64_PEAK_TFLOPS = 1.20  # measured FMA throughput (profiles/fp64_fma_peak_gb300.md); nominal 1.25
+# DRAM bytes (read + write) per launch of a stage's kernels from one ncu capture
+# (profiles/), keyed by stage and path, with the hash of the library sources
+# the capture was taken at: a stale entry (kernels changed since) reads as null.
+TRAFFIC = {}
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2003_11679_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(stage, path):
+    e = TRAFFIC.get((stage, path))
+    return e[0] if e and e[1] == source_hash() else None
+
 
 
 def run_ours(args):
@@ -174,6 +227,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     libbuild.build()
     wl = workload(args.workload)
+    fp64_peak, fp32_peak = sie.probe_fma(local)  # FMA throughput, measured here
     stream = torch.cuda.Stream()
     ctx = sie.Context(local, stream=stream.cuda_stream)
     mesh = sie.Mesh(ctx, wl["V"], wl["T"])
@@ -253,6 +307,7 @@ def run_ours(args):
         # current rows (the grid product lives there; the charge rows are exact in both)
         mixed_err = float((y[:ne] - y64[:ne]).abs().norm() / y64[:ne].abs().norm())
     solves = solve_stats(sie, ctx, args) if not args.no_solve else None
+    lossy_solves = lossy_solve_stats(sie, op, args, wl) if not args.no_solve else None
     ms, e2e_s = combine_ranks(ms, e2e_s, world, f"cuda:{local}")
     if rank != 0:
         return
@@ -269,14 +324,15 @@ def run_ours(args):
         avg_s = dms * 1e-3 / dcount
         gbs = B / avg_s / 1e9
         tfl = F / avg_s / 1e12
-        if tfl / FP64_PEAK_TFLOPS >= gbs / peaks["hbm_gbs"]:
-            roof = {"bound": "alu", "kernel": dom, "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_note": "FP64 FMA, measured (nominal 1.25 TFLOP/s)",
+        if tfl / fp64_peak >= gbs / peaks["hbm_gbs"]:
+            roof = {"bound": "alu", "kernel": dom, "achieved": tfl, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": tfl / fp64_peak, "traffic": traffic_of(dom, "fp64"),
+                    "peak_note": "FP64 FMA, measured in this run by sie_probe_fma (nominal 1.25 TFLOP/s)",
                     "hbm_gbs_achieved": gbs, "hbm_frac": gbs / peaks["hbm_gbs"]}
         else:
             roof = {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_note": f"HBM copy, {kind}"}
+                    "frac": gbs / peaks["hbm_gbs"], "traffic": traffic_of(dom, "fp64"),
+                    "peak_note": f"HBM copy, {kind}"}
         roof.update({"algorithmic_bytes": B, "algorithmic_flops": F, "avg_launch_us": avg_s * 1e6,
                      "launches": dcount})
     if graph_state & 1:
@@ -285,7 +341,7 @@ def run_ours(args):
         launches = args.steps * int(ginfo[17] + ginfo[18] * gstats["inner_iters_max"])
     else:
         launches = sum(c for _, c in prof.values())
-    cpu = cpu_baseline(wl, args) if not args.no_cpu and world == 1 else None  # rank 0 at N = 1 only
+    cpu = cpu_baseline(args) if not args.no_cpu and world == 1 else None  # rank 0 at N = 1 only
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -306,9 +362,11 @@ def run_ours(args):
                          "note": "timed loop replays one CUDA graph per product (nested solve as a device-ended "
                                  "loop); the stage breakdown comes from the stream path with per-stage events"},
         "solves": solves,
+        "solves_workload": lossy_solves,
         "mixed_precision": mixed_line(ne, args, ms32, prof32, mixed_err, info, peaks, kind),
         "stages_ms": {k: round(v[0], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
         "roofline": roof,
+        "fma_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak, "how": "sie_probe_fma, this run"},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
@@ -361,15 +419,62 @@ def _jsonable(o):
 
 
 def solve_stats(sie, ctx, args):
-    """GMRES solves of the dielectric sphere (1,920 RWG, eps_r = 4, 3 GHz) for
-    seeded incidence directions: solves/s, p50/p99 latency, iterations."""
-    from synth import cn_vector
-    wl = workload("dielectric-sphere-1920")
+    """GMRES solves of the dielectric sphere (1,920 RWG, eps_r = 4, 3 GHz, r = 1 cm,
+    equal-volume icosphere) for seeded incidence directions, to tol_outer 1e-6:
+    the FP64 solve and the mixed-precision refinement (SIE_SOLVE_REFINE) on the
+    same right-hand sides.  Each solve's backscatter RCS is compared with the
+    Mie series; solves/s counts every solve, `ok` those within 1% of Mie that
+    converged."""
+    name = "dielectric-sphere-1920"
+    wl = workload(name)
+    ref = mie_backscatter(name)
     mesh = sie.Mesh(ctx, wl["V"], wl["T"])
     op = sie.Operator(mesh, wl["f"], wl["eps_r"], 1.0, wl["sigma"], sie.params(tol_outer=1e-6))
     rng = np.random.default_rng(7)
-    lat, its = [], []
+    dirs = []
     for i in range(args.solves):
+        z = rng.uniform(-1, 1)
+        ph = rng.uniform(0, 2 * np.pi)
+        kh = np.array([np.sqrt(1 - z * z) * np.cos(ph), np.sqrt(1 - z * z) * np.sin(ph), z])
+        ep = np.cross(kh, [0.3, -0.5, 0.8])
+        dirs.append((kh, ep / np.linalg.norm(ep)))
+    out = {"workload": name, "tol": 1e-6, "solves": args.solves, "mie_backscatter_m2": ref}
+    xs = {}
+    for refine in (False, True):
+        lat, its, errs, conv = [], [], [], []
+        for i, (kh, ep) in enumerate(dirs):
+            b = op.rhs_planewave(kh, ep)
+            t0 = time.perf_counter()
+            x, it, rr = op.solve(b, check=False, refine=refine)
+            lat.append(time.perf_counter() - t0)
+            its.append(int(it[0]))
+            conv.append(bool(rr[0] < 1e-6))
+            errs.append(float(op.rcs(x, -kh)[0] / ref - 1.0))
+            xs[(refine, i)] = x
+        lat = np.array(lat)
+        ok = [c and abs(e) <= 0.01 for c, e in zip(conv, errs)]
+        out["refined" if refine else "fp64"] = {
+            "solves_per_s": float(len(lat) / lat.sum()), "ok_solves": int(sum(ok)), "not_converged": conv.count(False),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)), "iters": its,
+            "rcs_rel_err_vs_mie": errs}
+    out["refined_vs_fp64"] = {
+        "speedup": out["refined"]["solves_per_s"] / out["fp64"]["solves_per_s"],
+        "max_rel_diff_x": max(float(np.linalg.norm(xs[(True, i)] - xs[(False, i)]) / np.linalg.norm(xs[(False, i)]))
+                              for i in range(len(dirs)))}
+    op.close()
+    mesh.close()
+    return out
+
+
+def lossy_solve_stats(sie, op, args, wl):
+    """GMRES solves of the timed workload itself (FP64, tol_outer 1e-4, Sec. V)
+    for seeded incidence directions: solves/s, latency, iterations, and each
+    solve's backscatter RCS against the Mie series (ok: converged and within
+    1%)."""
+    ref = mie_backscatter(args.workload)
+    rng = np.random.default_rng(11)
+    lat, its, errs, conv = [], [], [], []
+    for i in range(args.lossy_solves):
         z = rng.uniform(-1, 1)
         ph = rng.uniform(0, 2 * np.pi)
         kh = np.array([np.sqrt(1 - z * z) * np.cos(ph), np.sqrt(1 - z * z) * np.sin(ph), z])
@@ -380,36 +485,77 @@ def solve_stats(sie, ctx, args):
         x, it, rr = op.solve(b, check=False)
         lat.append(time.perf_counter() - t0)
         its.append(int(it[0]))
-    op.close()
-    mesh.close()
+        conv.append(bool(rr[0] < op_tol(sie)))
+        errs.append(float(op.rcs(x, -kh)[0] / ref - 1.0))
+    st = op.stats()
     lat = np.array(lat)
-    return {"workload": "dielectric-sphere-1920", "tol": 1e-6, "solves": args.solves,
-            "solves_per_s": float(len(lat) / lat.sum()), "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "iters": [int(i) for i in its]}
+    return {"workload": args.workload, "tol": op_tol(sie), "solves": len(lat),
+            "solves_per_s": float(len(lat) / lat.sum()) if len(lat) else None,
+            "ok_solves": int(sum(c and abs(e) <= 0.01 for c, e in zip(conv, errs))),
+            "not_converged": conv.count(False), "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_s": float(np.percentile(lat, 99)) if len(lat) else None, "iters": its,
+            "rcs_rel_err_vs_mie": errs, "mie_backscatter_m2": ref, "last_solve_stats": st,
+            "dense_constraint_lu_ms": float(op.info()[19])}
 
 
-def cpu_baseline(wl, args):
-    """The oracle's FP64 AIM grid products on the host cores (bounded sample)."""
-    from oracle import aim
-    from oracle.rwg import Mesh
-    from synth import cn_vector
-    m = Mesh(wl["V"], wl["T"])
-    g = aim.grid_params(m, M=2, grid_n=wl["grid_n"] or None)
-    k0 = 2 * np.pi * wl["f"] / 299792458.0
-    A = aim.AIM(m, k0, g, near=False)
-    x = cn_vector(m.ne, 1)
-    reps = 0
-    t0 = time.perf_counter()
-    while True:
-        A.grid_L(x)
-        A.grid_K(x)
-        reps += 1
-        if time.perf_counter() - t0 > args.cpu_seconds or reps >= 50:
-            break
-    dt = (time.perf_counter() - t0) / reps
-    return {"value": m.ne / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"exterior grid products L0+K0 only (7 numpy FFT convolutions at the full grid), {reps} reps; "
-                      "near-region products excluded, so the CPU time per step is understated"}
+def op_tol(sie):
+    return sie.params().tol_outer
+
+
+class OracleStep:
+    """One step of the oracle on a bounded sample of a workload: the system
+    product of Eq. (sys) in its AIM form (oracle/system.AimGIBC: exterior AIM
+    products with their near corrections, near-region-only interior Z' by a
+    sparse LU; AIM interior for a dielectric) on a level-2 icosphere of the
+    same radius, material and exterior grid.  Set-up (near-region integrals,
+    factorisation) is not part of the step."""
+
+    def __init__(self, wl):
+        from oracle import aim, system
+        from oracle.rwg import Mesh
+        from synth import cn_vector, icosphere
+        V, T = icosphere(2, wl["radius"])
+        self.m = Mesh(V, T)
+        mfull = Mesh(wl["V"], wl["T"])
+        gfull = aim.grid_params(mfull, M=2, grid_n=wl["grid_n"] or None)
+        # the sample keeps the workload's grid spacing, extent and FFT size
+        g = aim.grid_params(self.m, M=2, h=gfull.h)
+        ki = system.k_medium(wl["f"], wl["eps_r"], wl["sigma"])
+        delta = 1.0 / abs(ki.imag) if ki.imag != 0 else np.inf
+        near = 5 * delta <= (g.Rnear - g.M) * g.h
+        self.S = system.AimGIBC(self.m, wl["f"], wl["eps_r"], wl["sigma"], g,
+                                interior="near" if near else "aim", cutoff=5 * delta if near else None)
+        self.H, self.rho = cn_vector(self.m.ne, 1), cn_vector(self.m.nt, 2)
+        self.grid_N, self.full_N = [int(v) for v in g.N], [int(v) for v in gfull.N]
+
+    def __call__(self):
+        return self.S.apply(self.H, self.rho)
+
+    def describe(self, ne_full):
+        return (f"oracle system product of Eq. (sys) (AIM exterior with near terms, near-only interior Z' by sparse "
+                f"LU) on a 320-triangle sample of the same sphere, material and exterior grid (N {self.grid_N} vs "
+                f"{self.full_N} of the full mesh: the same FFT size); value = {ne_full} RWG unknowns / step time, an "
+                f"upper bound of the oracle's full-size throughput (its grid part has the full size, its near and "
+                f"interior parts are smaller); numpy/scipy kernels, single-threaded")
+
+
+def cpu_baseline(args):
+    """The oracle's step (OracleStep) on the host: one warm-up, median of >= 5."""
+    wl = workload(args.workload)
+    step = OracleStep(wl)
+    step()
+    ts = []
+    t_end = time.perf_counter() + args.cpu_seconds
+    while len(ts) < 5 or (time.perf_counter() < t_end and len(ts) < 50):
+        t0 = time.perf_counter()
+        step()
+        ts.append(time.perf_counter() - t0)
+    med = float(np.median(ts))
+    model, ncpu = cpu_info()
+    ne_full = 3 * len(wl["T"]) // 2
+    return {"value": ne_full / med, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": step.describe(ne_full),
+            "median_step_s": med, "steps": len(ts), "cpu_model": model, "host_cpus": ncpu,
+            "sample_rwg": step.m.ne, "sample_value": step.m.ne / med}
 
 
 def run_reference(args):
@@ -417,17 +563,25 @@ def run_reference(args):
     if rank != 0:
         return
     wl = workload(args.workload)
+    t_wall = time.perf_counter()
+    step = OracleStep(wl)
+    for _ in range(args.warmup):
+        step()
     t0 = time.perf_counter()
-    cpu = cpu_baseline(wl, args)
-    line = {"metric": METRIC, "value": cpu["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * (1.5 * len(wl["T"])) / cpu["value"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
-            "data": "synthetic", "impl": "reference",
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    ne_full = 3 * len(wl["T"]) // 2
+    value = ne_full * args.steps / dt
+    model, ncpu = cpu_info()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "desc": wl["desc"]},
-            "cpu_baseline": {"kind": cpu["kind"], "cores": cpu["cores"], "sample": cpu["sample"],
-                             "value": cpu["value"]},
-            "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": time.perf_counter() - t0}
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": step.describe(ne_full), "value": value,
+                             "cpu_model": model, "host_cpus": ncpu},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_wall}
     print(json.dumps(line, default=_jsonable))
 
 
@@ -438,10 +592,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lossy-sphere-30720")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=30.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--solves", type=int, default=4)
+    ap.add_argument("--lossy-solves", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

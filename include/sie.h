@@ -115,6 +115,9 @@ typedef struct {
     double q_kres;        /* close if |k| (R_t + R_s) > q_kres (1.0)                    */
     double q_alen;        /* longest angular (asinh) panel (1.5)                        */
     double q_oratio;      /* outer panel ratio (0.25)                                   */
+    int dense_pc_max;     /* constraint preconditioners: factorise the triangle (charge)
+                             system densely on the GPU (complex64 LU) when N_t <= this
+                             (32768); else solve it iteratively                        */
 } sie_params;
 
 void sie_params_default(sie_params* p);
@@ -183,7 +186,10 @@ sie_status sie_op_stats(const sie_op* op, double out[6]);
  * +4 capture failed (the stream path is used); [17] nodes of the last
  * captured graph outside the nested loop (kernels, memsets, copies and the
  * loop node), [18] nodes of the loop body (run once per nested iteration);
- * [19] reserved (0). */
+ * [19] wall time in ms of the dense factorisations of the constraint
+ * preconditioners' triangle systems (0 when they are solved iteratively,
+ * minus the sie_status when the factorisation could not be made, e.g. -3 for
+ * no device memory; the iterative solve is used then). */
 sie_status sie_op_info(const sie_op* op, double info[20]);
 /* grid origin (3) and spacing of the exterior grid */
 sie_status sie_op_grid(const sie_op* op, double origin[3], double* h, int64_t N[3]);
@@ -276,6 +282,24 @@ sie_status sie_rcs(sie_op* op, const double* x, const double* rhat, int ndir, do
  * host.  No part of the array has to start at zero: a call writes every
  * direction, far-field sum and cross section that it reads back. */
 sie_status sie_rcs_static(sie_op* op, const double* x, const double* rhat, int ndir, double* rcs, int flags);
+
+/* x = A^-1 b for one dense complex matrix with the library's GPU LU, the one
+ * the constraint preconditioners use (Sec. III-D: the paper factorises its
+ * preconditioner by LU): complex64 blocked LU with partial pivoting, then two
+ * triangular solves, on device `device`.  A: n x n complex128 row-major
+ * (host), b, x: n complex128 (host); A and b are rounded to complex64, so x
+ * carries complex64 rounding amplified by the condition number.  Allocates
+ * and frees its device memory; synchronises.  SIE_ERR_ARG for n < 1 or a zero
+ * pivot (singular matrix). */
+sie_status sie_dense_solve(int device, int n, const double* A, const double* b, double* x);
+
+/* FMA throughput of device `device`: FP64 and FP32 TFLOP/s (2 flops per
+ * FMA), measured by the library's own probe kernel (independent FMA chains on
+ * every SM, best of three timed launches after a warm-up).  The paper has no
+ * counterpart: this is the arithmetic peak the FP64 path's roofline fractions
+ * are quoted against.  Allocates and frees a small device buffer; runs on the
+ * legacy default stream and synchronises it. */
+sie_status sie_probe_fma(int device, double* fp64_tflops, double* fp32_tflops);
 
 #ifdef __cplusplus
 }

@@ -439,3 +439,63 @@ def near_pairs(aim, g):
 def kappa(A, B):
     """Matrix error metric of Sec. IV: max|A - B| / max|A|."""
     return np.abs(A - B).max() / np.abs(A).max()
+
+
+# ---------------------------------------------------------------- sampled rows (large meshes)
+def near_pairs_of(aim, g, tris):
+    """The near pairs (t, s) of the AIM rule (Chebyshev distance of stencil
+    centres <= R_near) for the test triangles t in `tris` only, sorted."""
+    c = stencil_center(aim.base, g)
+    out = []
+    for t in sorted(set(int(v) for v in tris)):
+        d = np.abs(c - c[t]).max(axis=1)
+        out.extend((t, int(s)) for s in np.nonzero(d <= g.Rnear)[0])
+    return np.array(out, dtype=np.int64).reshape(-1, 2)
+
+
+def near_pairs_cutoff_of(m, cutoff, tris):
+    """near_pairs_cutoff restricted to the test triangles in `tris`."""
+    c = m.centroid
+    R = np.linalg.norm(m.V[m.T] - c[:, None, :], axis=2).max(1)
+    out = []
+    for t in sorted(set(int(v) for v in tris)):
+        gap = np.sqrt(((c - c[t]) ** 2).sum(1)) - R - R[t]
+        touch = np.isin(m.T, m.T[t]).any(axis=1)
+        out.extend((t, int(s)) for s in np.nonzero((gap <= cutoff) | touch)[0])
+    return np.array(out, dtype=np.int64).reshape(-1, 2)
+
+
+def _assemble_rows(m, rows, pairs, local):
+    """Dense rows (len(rows), ne) of an edge matrix from 3x3 local blocks of
+    triangle pairs: entry (m, n) sums block[i, j] over pairs (t, s) with edge m
+    in slot i of t and edge n in slot j of s."""
+    out = np.zeros((len(rows), m.ne), complex)
+    pos = {int(r): i for i, r in enumerate(rows)}
+    for p, (t, s) in enumerate(pairs):
+        for i in range(3):
+            r = pos.get(int(m.tri_edge[t, i]))
+            if r is None:
+                continue
+            for j in range(3):
+                out[r, m.tri_edge[s, j]] += local[p, i, j]
+    return out
+
+
+def near_rows(A, rows, quad=None):
+    """Rows of the precorrected exterior near matrices (NL, NK) of AIM operator
+    A for the edges in `rows` (exact local entries minus the grid's own)."""
+    m = A.mesh
+    tris = m.edge_tri[np.asarray(rows)].ravel()
+    pairs = near_pairs_of(A, A.g, tris)
+    t, s = pairs[:, 0], pairs[:, 1]
+    Le, Ke, _, _ = exact_local(m, A.k, t, s, quad)
+    Lg, Kg, _, _ = A.grid_local(t, s)
+    return _assemble_rows(m, rows, pairs, Le - Lg), _assemble_rows(m, rows, pairs, Ke - Kg)
+
+
+def near_only_rows(m, k, cutoff, rows, quad=None):
+    """Rows of the near-region-only interior matrices (L_NR, K_NR) for `rows`."""
+    tris = m.edge_tri[np.asarray(rows)].ravel()
+    pairs = near_pairs_cutoff_of(m, cutoff, tris)
+    L, K, _, _ = exact_local(m, complex(k), pairs[:, 0], pairs[:, 1], quad)
+    return _assemble_rows(m, rows, pairs, L), _assemble_rows(m, rows, pairs, K)

@@ -117,3 +117,112 @@ class DenseGIBC:
             + D.T @ (self.Lp0 @ (-m.area * c0rho))
         r2 = (D @ H) / m.area + 1j * self.k0 * c0rho
         return r1, r2
+
+
+# ---------------------------------------------------------------- AIM form of Eq. (sys) (oracle O2)
+def incidence_sparse(mesh):
+    """D (nt x ne) as a sparse matrix: D[p, n] = +l_n on T+, -l_n on T-."""
+    import scipy.sparse as sp
+    rows = np.repeat(np.arange(mesh.nt), 3)
+    cols = mesh.tri_edge.ravel()
+    vals = (mesh.tri_sign * mesh.edge_len[mesh.tri_edge]).ravel()
+    return sp.coo_matrix((vals, (rows, cols)), shape=(mesh.nt, mesh.ne)).tocsr()
+
+
+def Ix_sparse(mesh):
+    """I_x of mom.Ix (same closed form per triangle) as a sparse matrix."""
+    import scipy.sparse as sp
+    cf = mesh.coef()
+    rows, cols, vals = [], [], []
+    for i in range(3):
+        for j in range(3):
+            c = mesh.centroid
+            pi = mesh.V[mesh.tri_free[:, i]] - c
+            pj = mesh.V[mesh.tri_free[:, j]] - c
+            v = cf[:, i] * cf[:, j] * mesh.area * np.einsum("ta,ta->t", mesh.normal, np.cross(pj, pi))
+            rows.append(mesh.tri_edge[:, i])
+            cols.append(mesh.tri_edge[:, j])
+            vals.append(v)
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(mesh.ne, mesh.ne)).tocsr()
+
+
+def grid_LA(A, H):
+    """W G P H: the grid part of the vector-potential operator L_A (Eq. AIM_Lin
+    without its scalar term)."""
+    J, _ = A.project(H)
+    return A.interpolate(A._conv(J, A.kG), None, 0.0)
+
+
+def grid_Lphi(A, sig):
+    """Grid part of L_phi applied to triangle charges sig:
+    (1/A_p) sum_u w0[p,u] sum_v G(u - v) sum_q w0[q,v] sig_q / A_q."""
+    m = A.mesh
+    rho = np.zeros(A.Ng, complex)
+    np.add.at(rho, A.nodes.ravel(), (A.w0 * (sig / m.area)[:, None]).ravel())
+    Phi = A._conv(rho, A.kG)
+    return np.einsum("tu,tu->t", A.w0, Phi[A.nodes]) / m.area
+
+
+class AimGIBC:
+    """Eq. (sys) with every exterior operator in its AIM form (Eqs. AIM_Lin,
+    AIM_Kin and the near corrections of Eqs. LinNRP, KinNRP), the operators
+    of the GPU's system product:
+
+      row 1: j k0 L_A,AIM H - (K_0,AIM + Ix/2) Z' H + D^T L_phi,AIM B c0 rho
+      row 2: F D H + j k0 c0 rho,
+
+    and Z' = -(j k0 eps_r + sigma eta0)^-1 L_i^-1 (K_i - Ix/2) (Eq. GIBCdef / eta0)
+    with the interior operators near-region only (the 5-skin-depth rule of
+    Sec. V; L_i,NR factorised by a sparse LU, Eq. nest2pc solved exactly) or in
+    their AIM form on the same grid (formed column by column, dense LU)."""
+
+    def __init__(self, mesh, f, eps_r, sigma, g, interior="near", cutoff=None, quad=None):
+        import scipy.sparse.linalg as spl
+        self.mesh, self.f, self.eps_r, self.sigma = mesh, f, eps_r, sigma
+        self.k0 = 2 * np.pi * f / C0
+        self.ki = k_medium(f, eps_r, sigma)
+        self.ext = aim.AIM(mesh, self.k0, g, quad)
+        self.Ix = Ix_sparse(mesh)
+        self.D = incidence_sparse(mesh)
+        self.zs = zscale(f, eps_r, sigma)
+        if interior == "near":
+            self.inn = aim.NearOnly(mesh, self.ki, cutoff, quad)
+            self._lu = spl.splu(self.inn.NL.tocsc())
+            self._Ki = self.inn.NK
+        else:
+            self.inn = aim.AIM(mesh, self.ki, g, quad)
+            n = mesh.ne
+            Li = np.zeros((n, n), complex)
+            Ki = np.zeros((n, n), complex)
+            for c in range(n):
+                e = np.zeros(n)
+                e[c] = 1.0
+                Li[:, c] = self.inn.L(e)
+                Ki[:, c] = self.inn.K(e)
+            import scipy.linalg as sla
+            self._lu_dense = sla.lu_factor(Li)
+            self._Ki = Ki
+
+    def Z(self, H):
+        rhs = self._Ki @ H - 0.5 * (self.Ix @ H)
+        if hasattr(self, "_lu"):
+            y = self._lu.solve(rhs)
+        else:
+            import scipy.linalg as sla
+            y = sla.lu_solve(self._lu_dense, rhs)
+        return -y / self.zs
+
+    def LA(self, H):
+        return self.ext.NLA @ H + grid_LA(self.ext, H)
+
+    def Lphi(self, sig):
+        return self.ext.NLphi @ sig + grid_Lphi(self.ext, sig)
+
+    def apply(self, H, c0rho):
+        m = self.mesh
+        E = self.Z(H)
+        r1 = 1j * self.k0 * self.LA(H) - self.ext.K(E) - 0.5 * (self.Ix @ E) \
+            + self.D.T @ self.Lphi(-m.area * c0rho)
+        r2 = (self.D @ H) / m.area + 1j * self.k0 * c0rho
+        return r1, r2

@@ -33,7 +33,8 @@ SYMBOLS = ["sie_params_default", "sie_ctx_create", "sie_ctx_destroy", "sie_last_
            "sie_profile_read", "sie_mesh_create",
            "sie_mesh_destroy", "sie_mesh_counts", "sie_op_build", "sie_op_destroy", "sie_op_set_solver",
            "sie_op_stats", "sie_op_info", "sie_op_grid",
-           "sie_matvec", "sie_op_near_csr", "sie_rhs_planewave", "sie_solve", "sie_rcs", "sie_rcs_static"]
+           "sie_matvec", "sie_op_near_csr", "sie_rhs_planewave", "sie_solve", "sie_rcs", "sie_rcs_static",
+           "sie_probe_fma", "sie_dense_solve"]
 
 
 class sie_params(ctypes.Structure):
@@ -47,7 +48,7 @@ class sie_params(ctypes.Structure):
                 ("q_npan", ctypes.c_int), ("q_opan", ctypes.c_int), ("q_olam", ctypes.c_int),
                 ("q_omu", ctypes.c_int), ("q_emupan", ctypes.c_int), ("q_emu", ctypes.c_int),
                 ("q_ratio", ctypes.c_double), ("q_cf", ctypes.c_double), ("q_kres", ctypes.c_double),
-                ("q_alen", ctypes.c_double), ("q_oratio", ctypes.c_double)]
+                ("q_alen", ctypes.c_double), ("q_oratio", ctypes.c_double), ("dense_pc_max", ctypes.c_int)]
 
 
 class SieError(RuntimeError):
@@ -87,6 +88,8 @@ def lib():
         L.sie_solve.argtypes = [P, P, P, I, P, P, I]
         L.sie_rcs.argtypes = [P, P, P, I, P, I]
         L.sie_rcs_static.argtypes = [P, P, P, I, P, I]
+        L.sie_probe_fma.argtypes = [I, P, P]
+        L.sie_dense_solve.argtypes = [I, I, P, P, P]
         for name in SYMBOLS:
             f = getattr(L, name)
             if name not in ("sie_params_default", "sie_last_error"):
@@ -98,6 +101,23 @@ def lib():
 def _check(code):
     if code != SIE_OK:
         raise SieError(code, lib().sie_last_error().decode())
+
+
+def probe_fma(device=0):
+    """(FP64, FP32) FMA throughput in TFLOP/s measured on `device` by the library."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().sie_probe_fma(device, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def dense_solve(A, b, device=0):
+    """x = A^-1 b with the library's GPU complex64 LU (verification of the
+    factorisation the constraint preconditioners use)."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    b = np.ascontiguousarray(b, dtype=np.complex128)
+    x = np.zeros_like(b)
+    _check(lib().sie_dense_solve(device, len(b), A.ctypes.data, b.ctypes.data, x.ctypes.data))
+    return x
 
 
 def params(**kw):

@@ -1131,6 +1131,7 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
         return fail(SIE_ERR_OOM);
     }
     if ((s = sys_prepare(op)) != SIE_OK) return fail(s);
+    if ((s = constraint_lu_build(op)) != SIE_OK) return fail(s);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         set_error(std::string("sie_op_build: ") + cudaGetErrorString(e));

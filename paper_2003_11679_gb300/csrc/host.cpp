@@ -440,6 +440,7 @@ void sie_params_default(sie_params* p)
     p->q_kres = 1.0;
     p->q_alen = 1.5;
     p->q_oratio = 0.25;
+    p->dense_pc_max = 32768;
 }
 
 const char* sie_last_error(void) { return g_err.c_str(); }
@@ -562,7 +563,7 @@ sie_status sie_op_info(const sie_op* op, double info[20])
     info[16] = (op->gexec[0] ? 1.0 : 0.0) + (op->gexec[1] ? 2.0 : 0.0) + (op->gfailed ? 4.0 : 0.0);
     info[17] = (double)op->gnodes[0];
     info[18] = (double)op->gnodes[1];
-    info[19] = 0.0;
+    info[19] = op->lu_ms;
     return SIE_OK;
 }
 

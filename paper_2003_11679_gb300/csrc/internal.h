@@ -108,6 +108,25 @@ struct QuadDev {
 enum { QR_FAR = 0, QR_OUT, QR_ANG, QR_RAD, QR_OLAM, QR_OMU, QR_EMU };
 void make_quad(const sie_params& p, QuadDev& q);
 
+// Dense complex64 LU (partial pivoting) of a triangle system, on the device
+struct DenseLU {
+    int n = 0, nblk = 0, epoch = 0;
+    float2* A = nullptr;      // n x n row-major: the matrix, then its L and U factors
+    float2* invL = nullptr;   // inverses of the unit-lower diagonal blocks (nblk x 64 x 64)
+    float2* invU = nullptr;   // inverses of the upper diagonal blocks
+    int* ipiv = nullptr;      // row swaps of the factorisation
+    int* perm = nullptr;      // the resulting row permutation as a gather
+    int* flags = nullptr;     // 2 nblk: per-block completion flags of the two triangular solves
+    int* counter = nullptr;   // 2: ticket counters of the two triangular solves
+    int* err = nullptr;       // 1: a triangular-solve wait ran out; 2: zero pivot
+    float2 *y0 = nullptr, *y1 = nullptr, *prow = nullptr;
+    sie_status alloc(int n_);
+    void release();
+    sie_status factor(cudaStream_t st);
+    sie_status solve(cudaStream_t st, const double2* b, double2* x);
+    sie_status check(cudaStream_t st);
+};
+
 // One operator (one medium, one grid or near only)
 struct AimOp {
     double kr = 0, ki = 0;          // wavenumber k = kr + j ki
@@ -139,6 +158,8 @@ struct AimOp {
     float2* valLA32 = nullptr;
     float2* valK32 = nullptr;
     float2* valLphi32 = nullptr;
+    // dense LU of the constraint triangle system (null: iterative constraint solve)
+    DenseLU* lu = nullptr;
 };
 
 struct Workspace {
@@ -242,6 +263,7 @@ struct sie_op {
     double* gstat = nullptr;        // device: max nested iterations and residual of graph runs
     size_t gnodes[2] = {0, 0};      // nodes of the last captured graph: outside the loop, loop body
     double2* ir_buf = nullptr;      // iterative refinement: residual, correction, product (3 (ne + nt))
+    double lu_ms = 0;               // wall time of the dense constraint-preconditioner factorisations
 };
 
 // ------------------------------------------------------------------ launchers (aim.cu, near.cu)
@@ -276,6 +298,13 @@ sie_status nested_clear(sie_op* op);
 sie_status nested_check(sie_op* op, const char* who);
 double sys_rcs_scale(const sie_op* op);
 // nbatch consecutive grids (buf + k n^3, src + k N^3) in one launch per pass
+// T = I - kappa D diag(LA)^-1 D^T Lphi_NR into f.A (f allocated for N_t)
+sie_status dense_lu_assemble(cudaStream_t st, DenseLU& f, const sie_op* op, const AimOp& a, double2 kappa);
+// build (assemble + factorise) the dense constraint LUs of op (ext, and inn when it has a grid)
+sie_status constraint_lu_build(sie_op* op);
+void constraint_lu_release(sie_op* op);
+// SIE_ERR_TIMEOUT when a triangular-solve wait of a constraint LU ran out (synchronises)
+sie_status constraint_lu_check(sie_op* op);
 sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune,
                  sie_ctx* prof_ctx, int nbatch = 1);
 sie_status fft3d(cudaStream_t st, float2* buf, const float2* src, const GridDesc& g, int dir, int prune,

@@ -6,6 +6,7 @@
 // classical Gram-Schmidt (twice), plane-wave right-hand sides and the far
 // field / RCS of the solution.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -203,7 +204,8 @@ __global__ void k_gm_start(int64_t n, const double2* __restrict__ r, const doubl
                            double2* __restrict__ V0, double2* __restrict__ g, int m, double* __restrict__ sc,
                            int set_bnorm)
 {
-    double beta = sqrt(fmax(dot2[0].x, 0.0));
+    const double d2 = dot2[0].x;
+    const double beta = d2 != d2 ? d2 : sqrt(fmax(d2, 0.0));  // a NaN norm stays NaN (reported by the host)
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         double s = beta > 0 ? 1.0 / beta : 0.0;
@@ -250,7 +252,7 @@ __device__ void gm_givens(int j, int m, double2* __restrict__ H, double2* __rest
     double2 t = cm(cj(s), gj);
     g[j] = make_double2(c.x * gj.x, c.x * gj.y);
     g[j + 1] = make_double2(-t.x, -t.y);
-    sc[3 + j] = (sc[0] > 0) ? hypot(g[j + 1].x, g[j + 1].y) / sc[0] : 0.0;
+    sc[3 + j] = (sc[0] > 0) ? hypot(g[j + 1].x, g[j + 1].y) / sc[0] : (sc[0] == sc[0] ? 0.0 : sc[0]);
 }
 
 // Fused classical Gram-Schmidt, two passes.  The rows are split into
@@ -1420,12 +1422,19 @@ static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork&
         SIE_CUDA_TRY(cudaMemcpyAsync(out, x, sizeof(double2) * nt, cudaMemcpyDeviceToDevice, st));
         return SIE_OK;
     };
+    // with a dense LU of the triangle system (complex64) it preconditions the
+    // GMRES, which then needs a few iterations; without it, the identity
+    auto LU = [&](const double2* x, double2* out) {
+        Stage s_(c, "constraint_lu_solve");
+        return a.lu->solve(st, x, out);
+    };
+    const Apply P = a.lu ? Apply(LU) : Apply(I);
     int it = 0;
     double rr = 0;
     sie_status s;
     {
         Stage s_(c, "constraint_solve");
-        s = fgmres(c, K, nt, S, I, rq, q, tol, op->p.constraint_maxit, op->p.constraint_restart, &it, &rr);
+        s = fgmres(c, K, nt, S, P, rq, q, tol, op->p.constraint_maxit, op->p.constraint_restart, &it, &rr);
     }
     op->stats[4] = std::max(op->stats[4], (double)it);
     op->stats[5] = std::max(op->stats[5], rr);
@@ -1473,6 +1482,51 @@ static sie_status precond_sys(sie_op* op, const double2* x, double2* y)
     SIE_CUDA_TRY(cudaGetLastError());
     SIE_CUDA_TRY(cudaMemcpyAsync(y + ne, x + ne, sizeof(double2) * nt, cudaMemcpyDeviceToDevice, st));
     SIE_TRY(axpby(st, nt, -1.0 / jk0, ph, 1.0 / jk0, y + ne));
+    return SIE_OK;
+}
+
+sie_status constraint_lu_build(sie_op* op)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const int nt = (int)op->mesh->h.nt;
+    if (op->p.dense_pc_max <= 0 || nt > op->p.dense_pc_max) return SIE_OK;
+    auto t0 = std::chrono::steady_clock::now();
+    sie_status s = SIE_OK;
+    for (AimOp* a : {&op->ext, &op->inn}) {
+        if (a == &op->inn && !op->inn.has_grid) continue;  // near-only interiors use the SPAI
+        cplx k(a->kr, a->ki);
+        cplx kappa = 1.0 / (k * k);
+        a->lu = new DenseLU();
+        if ((s = a->lu->alloc(nt)) != SIE_OK) break;
+        if ((s = dense_lu_assemble(st, *a->lu, op, *a, make_double2(kappa.real(), kappa.imag()))) != SIE_OK) break;
+        if ((s = a->lu->factor(st)) != SIE_OK) break;
+    }
+    if (s != SIE_OK) {
+        // no room or a singular triangle system: the iterative constraint solve stays
+        cudaGetLastError();
+        cudaStreamSynchronize(st);
+        constraint_lu_release(op);
+        op->lu_ms = -(double)s;
+        return SIE_OK;
+    }
+    op->lu_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return SIE_OK;
+}
+
+void constraint_lu_release(sie_op* op)
+{
+    for (AimOp* a : {&op->ext, &op->inn})
+        if (a->lu) {
+            a->lu->release();
+            delete a->lu;
+            a->lu = nullptr;
+        }
+}
+
+sie_status constraint_lu_check(sie_op* op)
+{
+    for (AimOp* a : {&op->ext, &op->inn})
+        if (a->lu) SIE_TRY(a->lu->check(op->mesh->ctx->stream));
     return SIE_OK;
 }
 
@@ -1537,6 +1591,8 @@ void sys_release(sie_op* op)
 {
     cudaStream_t st = op->mesh->ctx->stream;
     sys_graph_reset(op);
+    cudaStreamSynchronize(st);
+    constraint_lu_release(op);
     for (cudaStream_t& g : op->gs)
         if (g) {
             cudaStreamDestroy(g);
@@ -1603,6 +1659,7 @@ sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, doubl
     if (iters) *iters = it;
     if (relres) *relres = rr;
     if (s == SIE_OK) s = nested_check(op, "sie_solve");
+    if (s == SIE_OK || s == SIE_ERR_NOT_CONVERGED) SIE_TRY(constraint_lu_check(op));
     return s;
 }
 
@@ -1680,6 +1737,7 @@ sie_status sys_solve_refined(sie_op* op, const double2* b, double2* x, int* iter
     op->stats[1] = rel;
     if (iters) *iters = total;
     if (relres) *relres = rel;
+    SIE_TRY(constraint_lu_check(op));
     if (!(rel < op->p.tol_outer)) return SIE_ERR_NOT_CONVERGED;
     return nested_check(op, "sie_solve (refined)");
 }

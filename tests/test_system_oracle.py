@@ -77,3 +77,54 @@ def test_lossy_near_only_interior_rcs():
     got = system.rcs(m, S.k0, H, E, [[0, 0, 1]])[0]
     ref = mie.backscatter_rcs(1e-3, 10e9, 1.0, 1e4)
     assert abs(got / ref - 1) < 0.01
+
+
+@pytest.fixture(scope="module")
+def aimsys():
+    """Conductive sphere (1e4 S/m, 10 GHz, r = 1 mm, 80 triangles): the AIM form
+    of Eq. (sys) (oracle O2) beside the dense form, both with the near-region-only
+    interior of the 5-skin-depth rule."""
+    from oracle import aim
+    V, T = icosphere(1, 1e-3, equal_volume=True)
+    m = Mesh(V, T)
+    ki = system.k_medium(10e9, 1.0, 1e4)
+    cut = 5.0 / abs(ki.imag)
+    g = aim.grid_params(m, M=2)
+    return m, system.AimGIBC(m, 10e9, 1.0, 1e4, g, interior="near", cutoff=cut), \
+        system.DenseGIBC(m, 10e9, 1.0, 1e4, interior="near", cutoff=cut)
+
+
+def test_aim_system_scalar_split_is_aim_L(aimsys):
+    """L_A,AIM - k0^-2 D^T L_phi,AIM D equals the oracle's one-pass AIM product
+    L_AIM (Eq. AIM_Lin): pins the separate vector and scalar grid paths and the
+    triangle near correction of L_phi against the combined path."""
+    m, S, _ = aimsys
+    H = cn_vector(m.ne, 31)
+    split = S.LA(H) - (S.D.T @ S.Lphi(S.D @ H)) / S.k0 ** 2
+    ref = S.ext.L(H)
+    assert np.linalg.norm(split - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_aim_system_interior_and_rows(aimsys):
+    """Z' by the sparse LU equals the dense solve; the charge rows are exact; the
+    current rows match the dense system to the AIM approximation error."""
+    m, S, Dn = aimsys
+    H, rho = cn_vector(m.ne, 32), cn_vector(m.nt, 33)
+    assert np.linalg.norm(S.Z(H) - Dn.Z @ H) <= 1e-12 * np.linalg.norm(Dn.Z @ H)
+    r1, r2 = S.apply(H, rho)
+    d1, d2 = Dn.sys_apply(H, rho)
+    assert np.linalg.norm(r2 - d2) <= 1e-13 * np.linalg.norm(d2)
+    assert np.linalg.norm(r1 - d1) <= 2e-3 * np.linalg.norm(d1)
+
+
+def test_stored_mie_backscatter_is_the_oracle():
+    """tests/golden/mie_backscatter.txt (read by bench.py to check its solves)
+    holds what oracle/mie.py gives."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+    import make_mie_backscatter as g
+    stored = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden", "mie_backscatter.txt"))
+              if not l.startswith("#")]
+    for row, s in zip(g.rows(), stored):
+        assert row[0] == s[0] and abs(row[5] - float(s[5])) <= 1e-15 * row[5]
