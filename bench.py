@@ -45,12 +45,17 @@ UNIT = "RWG-unknown matvecs/s"
 L2_BYTES = 129 * 2 ** 20
 
 
+LOSSY_LEVELS = {"lossy-sphere-30720": 5, "lossy-sphere-7680": 4, "lossy-sphere-1920": 3, "lossy-sphere-480": 2}
+
+
 def workload(name):
     from synth import icosphere
-    if name == "lossy-sphere-30720":
-        V, T = icosphere(5, 1e-3)
-        return dict(V=V, T=T, f=10e9, eps_r=1.0, sigma=5.8e7, grid_n=64, radius=1e-3, level=5,
-                    desc="copper sphere r=1mm, sigma=5.8e7 S/m, 10 GHz, 20480 triangles / 30720 RWG, "
+    if name in LOSSY_LEVELS:
+        lev = LOSSY_LEVELS[name]
+        V, T = icosphere(lev, 1e-3)
+        nt = 20 * 4 ** lev
+        return dict(V=V, T=T, f=10e9, eps_r=1.0, sigma=5.8e7, grid_n=64, radius=1e-3, level=lev,
+                    desc=f"copper sphere r=1mm, sigma=5.8e7 S/m, 10 GHz, {nt} triangles / {3 * nt // 2} RWG, "
                          "grid 63^3 (grid_n 64, FFT 128^3), complex128, near-only interior, 1 RHS")
     if name == "dielectric-sphere-1920":
         V, T = icosphere(3, 1e-2, equal_volume=True)
@@ -63,6 +68,8 @@ def workload(name):
 def mie_backscatter(name):
     """The Mie-series backscatter RCS of a workload's sphere, as stored by
     tests/golden/make_mie_backscatter.py (from the oracle's Mie series)."""
+    if name in LOSSY_LEVELS:
+        name = "lossy-sphere-30720"  # the same sphere at every mesh level
     path = os.path.join(ROOT, "tests", "golden", "mie_backscatter.txt")
     for line in open(path):
         f = line.split()
@@ -232,7 +239,9 @@ def run_ours(args):
     ctx = sie.Context(local, stream=stream.cuda_stream)
     mesh = sie.Mesh(ctx, wl["V"], wl["T"])
     t0 = time.time()
-    op = sie.Operator(mesh, wl["f"], wl["eps_r"], 1.0, wl["sigma"], sie.params(grid_n=wl["grid_n"]))
+    model = sie.SIE_SIBC if args.interior == "sibc" else sie.SIE_GIBC
+    op = sie.Operator(mesh, wl["f"], wl["eps_r"], 1.0, wl["sigma"],
+                      sie.params(grid_n=wl["grid_n"], interior_model=model))
     build_s = time.time() - t0
     info = op.info()
     ne, nt = mesh.ne, mesh.nt
@@ -346,7 +355,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": wl["desc"], "ne": ne, "nt": nt,
+        "config": {"workload": args.workload, "desc": wl["desc"], "interior": args.interior, "ne": ne, "nt": nt,
                    "grid_N": info[0:3].tolist(), "fft_n": info[3:6].tolist(), "near_nnz_ext": int(info[8]),
                    "near_nnz_int": int(nnz_int), "step": "system matvec, Eq. (sys) (AEFIE, [H; c0 rho])",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
@@ -597,6 +606,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--solves", type=int, default=4)
     ap.add_argument("--lossy-solves", type=int, default=3)
+    ap.add_argument("--interior", default="gibc", choices=["gibc", "sibc"],
+                    help="interior model of the timed operator (sibc: the surface impedance comparator)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -66,6 +66,7 @@ typedef struct sie_mesh sie_mesh;
 typedef struct sie_op sie_op;
 
 enum { SIE_FP64 = 0, SIE_MIXED = 1 };          /* grid-path precision */
+enum { SIE_GIBC = 0, SIE_SIBC = 1 };           /* interior model (sie_params.interior_model) */
 enum { SIE_DEVICE_PTRS = 1,                    /* flags: vector args are device pointers */
        SIE_SOLVE_REFINE = 2 };                  /* sie_solve: mixed-precision iterative refinement */
 
@@ -118,6 +119,11 @@ typedef struct {
     int dense_pc_max;     /* constraint preconditioners: factorise the triangle (charge)
                              system densely on the GPU (complex64 LU) when N_t <= this
                              (32768); else solve it iteratively                        */
+    int interior_model;   /* SIE_GIBC (default): Z_i from the interior operators
+                             (Eqs. GIBCdef, nest02, nest2); SIE_SIBC: the surface
+                             impedance boundary condition the paper compares against
+                             (Sec. I-II), Z' = (eta_i / eta0) G^-1 I_x with the RWG
+                             Gram matrix G (no interior operators are built)          */
 } sie_params;
 
 void sie_params_default(sie_params* p);
@@ -163,8 +169,9 @@ sie_status sie_op_destroy(sie_op* op);
  * complex64 copies of the FP64-integrated values (FP32 products, FP64 row
  * sums), FP64 interior (lossy-medium) products and FP64 Krylov), tol_outer,
  * tol_inner, maxit, restart, inner_maxit, tol_constraint, constraint_maxit,
- * constraint_restart and tol_constraint_inner are taken from params; grid and
- * quadrature fields are ignored (they are fixed at build time). */
+ * constraint_restart and tol_constraint_inner are taken from params; grid,
+ * quadrature, dense_pc_max and interior_model are ignored (they are fixed at
+ * build time). */
 sie_status sie_op_set_solver(sie_op* op, const sie_params* params);
 
 /* Statistics of the last sie_solve on this operator (6 doubles): outer

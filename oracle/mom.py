@@ -189,3 +189,22 @@ def Ix(mesh):
                 val = cf[t, i] * cf[t, j] * mesh.area[t] * (mesh.normal[t] @ np.cross(p[j], p[i]))
                 X[mesh.tri_edge[t, i], mesh.tri_edge[t, j]] += val
     return X
+
+
+def gram(mesh):
+    """RWG Gram matrix G_mn = I f_m . f_n dS (dense).  On triangle t with centroid
+    c, f_i = c_i (r - p_i) = c_i ((r - c) + (c - p_i)), and I (r - c) dS = 0,
+    I |r - c|^2 dS = A (l_1^2 + l_2^2 + l_3^2) / 36, so the 3 x 3 block is
+    c_i c_j A [(l_1^2 + l_2^2 + l_3^2) / 36 + (c - p_i).(c - p_j)]."""
+    ne = mesh.ne
+    G = np.zeros((ne, ne))
+    cf = mesh.coef()
+    for t in range(mesh.nt):
+        c = mesh.centroid[t]
+        v = mesh.V[mesh.T[t]]
+        l2 = sum(np.sum((v[(i + 1) % 3] - v[i]) ** 2) for i in range(3))
+        q = c - mesh.V[mesh.tri_free[t]]
+        for i in range(3):
+            for j in range(3):
+                G[mesh.tri_edge[t, i], mesh.tri_edge[t, j]] += cf[t, i] * cf[t, j] * mesh.area[t] * (l2 / 36.0 + q[i] @ q[j])
+    return G

@@ -59,6 +59,22 @@ def z_dense(mesh, f, eps_r, sigma, Li, Ki, Ix):
     return -np.linalg.solve(Li, Ki - 0.5 * Ix) / zscale(f, eps_r, sigma)
 
 
+def eta_medium(f, eps_r, sigma, mu_r=1.0):
+    """Wave impedance of the object's medium, eta_i = sqrt(j w mu / (sigma + j w eps)),
+    branch Re eta_i > 0."""
+    w = 2 * np.pi * f
+    eta = np.sqrt(1j * w * MU0 * mu_r / (sigma + 1j * w * EPS0 * eps_r) + 0j)
+    return -eta if eta.real < 0 else eta
+
+
+def z_sibc(mesh, f, eps_r, sigma, G, Ix):
+    """Surface impedance boundary condition (the high-conductivity limit the
+    paper compares against): n x E = eta_i n x (n x H) on the surface, i.e.
+    the coefficients of n x E and n x H satisfy G E = eta_i Ix H with the RWG
+    Gram matrix G; divided by eta0: Z'_SIBC = (eta_i / eta0) G^-1 Ix."""
+    return eta_medium(f, eps_r, sigma) / ETA0 * np.linalg.solve(G, Ix)
+
+
 def far_vectors(mesh, k0, rhat, p=6):
     """F[n, d, a] = I f_n . e_a exp(j k0 rhat_d . r) dS (ne, ndir, 3)."""
     pts, wts = aim.tri_rule_pts(mesh, p)
@@ -95,14 +111,18 @@ class DenseGIBC:
         self.LA0, self.Lp0, self.K0 = LA0, Lp0, K0
         self.L0 = mom.L_full(mesh, LA0, Lp0, self.k0)
         self.Ix = mom.Ix(mesh)
-        if interior == "dense":
-            LAi, Lpi, Ki = mom.dense(mesh, self.ki, quad)
-            Li = mom.L_full(mesh, LAi, Lpi, self.ki)
-        else:  # near-region-only interior with the skin-depth cutoff (Sec. V)
-            no = aim.NearOnly(mesh, self.ki, cutoff, quad)
-            Li, Ki = no.NL.toarray(), no.NK.toarray()
-        self.Li, self.Ki = Li, Ki
-        self.Z = z_dense(mesh, f, eps_r, sigma, Li, Ki, self.Ix)
+        if interior == "sibc":
+            self.Li = self.Ki = None
+            self.Z = z_sibc(mesh, f, eps_r, sigma, mom.gram(mesh), self.Ix)
+        else:
+            if interior == "dense":
+                LAi, Lpi, Ki = mom.dense(mesh, self.ki, quad)
+                Li = mom.L_full(mesh, LAi, Lpi, self.ki)
+            else:  # near-region-only interior with the skin-depth cutoff (Sec. V)
+                no = aim.NearOnly(mesh, self.ki, cutoff, quad)
+                Li, Ki = no.NL.toarray(), no.NK.toarray()
+            self.Li, self.Ki = Li, Ki
+            self.Z = z_dense(mesh, f, eps_r, sigma, Li, Ki, self.Ix)
         self.A = 1j * self.k0 * self.L0 - (K0 + 0.5 * self.Ix) @ self.Z
 
     def solve(self, b):
@@ -174,10 +194,12 @@ class AimGIBC:
 
     and Z' = -(j k0 eps_r + sigma eta0)^-1 L_i^-1 (K_i - Ix/2) (Eq. GIBCdef / eta0)
     with the interior operators near-region only (the 5-skin-depth rule of
-    Sec. V; L_i,NR factorised by a sparse LU, Eq. nest2pc solved exactly) or in
-    their AIM form on the same grid (formed column by column, dense LU)."""
+    Sec. V; L_i,NR factorised by a sparse LU, Eq. nest2pc solved exactly), in
+    their AIM form on the same grid (formed column by column, dense LU), or the
+    surface impedance condition Z' = (eta_i / eta0) G^-1 Ix (interior="sibc")."""
 
     def __init__(self, mesh, f, eps_r, sigma, g, interior="near", cutoff=None, quad=None):
+        import scipy.sparse as sp
         import scipy.sparse.linalg as spl
         self.mesh, self.f, self.eps_r, self.sigma = mesh, f, eps_r, sigma
         self.k0 = 2 * np.pi * f / C0
@@ -186,7 +208,10 @@ class AimGIBC:
         self.Ix = Ix_sparse(mesh)
         self.D = incidence_sparse(mesh)
         self.zs = zscale(f, eps_r, sigma)
-        if interior == "near":
+        if interior == "sibc":
+            self._sibc = eta_medium(f, eps_r, sigma) / ETA0
+            self._lu_gram = spl.splu(sp.csc_matrix(mom.gram(mesh)))
+        elif interior == "near":
             self.inn = aim.NearOnly(mesh, self.ki, cutoff, quad)
             self._lu = spl.splu(self.inn.NL.tocsc())
             self._Ki = self.inn.NK
@@ -205,6 +230,8 @@ class AimGIBC:
             self._Ki = Ki
 
     def Z(self, H):
+        if hasattr(self, "_sibc"):
+            return self._sibc * self._lu_gram.solve(self.Ix @ H)
         rhs = self._Ki @ H - 0.5 * (self.Ix @ H)
         if hasattr(self, "_lu"):
             y = self._lu.solve(rhs)

@@ -20,6 +20,7 @@ _lib = None
 SIE_OK = 0
 SIE_ERR_NOT_CONVERGED = 5
 SIE_FP64, SIE_MIXED = 0, 1
+SIE_GIBC, SIE_SIBC = 0, 1
 SIE_DEVICE_PTRS = 1
 SIE_SOLVE_REFINE = 2
 SIE_RCS_STATIC_MAX_DIR = 2048
@@ -48,7 +49,8 @@ class sie_params(ctypes.Structure):
                 ("q_npan", ctypes.c_int), ("q_opan", ctypes.c_int), ("q_olam", ctypes.c_int),
                 ("q_omu", ctypes.c_int), ("q_emupan", ctypes.c_int), ("q_emu", ctypes.c_int),
                 ("q_ratio", ctypes.c_double), ("q_cf", ctypes.c_double), ("q_kres", ctypes.c_double),
-                ("q_alen", ctypes.c_double), ("q_oratio", ctypes.c_double), ("dense_pc_max", ctypes.c_int)]
+                ("q_alen", ctypes.c_double), ("q_oratio", ctypes.c_double), ("dense_pc_max", ctypes.c_int),
+                ("interior_model", ctypes.c_int)]
 
 
 class SieError(RuntimeError):

@@ -1042,6 +1042,11 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
         op->p = *params;
     else
         sie_params_default(&op->p);
+    if (op->p.interior_model != SIE_GIBC && op->p.interior_model != SIE_SIBC) {
+        delete op;
+        set_error("sie_op_build: interior_model must be SIE_GIBC or SIE_SIBC");
+        return SIE_ERR_ARG;
+    }
     op->freq = freq_hz;
     op->eps_r = eps_r;
     op->mu_r = mu_r;
@@ -1106,7 +1111,16 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
     op->inn.g = g;
     double delta = ki.imag() < 0 ? -1.0 / ki.imag() : 1e300;
     double cut = op->p.skin_cutoff * delta;
-    if (cut <= (g.Rnear - g.M) * g.h) {
+    {
+        // eta_i / eta0 = sqrt(mu_r / eps~_r), eps~_r = eps_r - j sigma / (w eps0), branch Re > 0
+        std::complex<double> eta = std::sqrt(std::complex<double>(mu_r) / std::complex<double>(eps_r, -sigma / (w * eps0)));
+        if (eta.real() < 0) eta = -eta;
+        op->eta_re = eta.real();
+        op->eta_im = eta.imag();
+    }
+    if (op->p.interior_model == SIE_SIBC) {
+        op->inn.has_grid = false;  // no interior operators: Z' comes from the Gram system
+    } else if (cut <= (g.Rnear - g.M) * g.h) {
         op->inn.has_grid = false;
         near_pairs_cutoff(mesh->h, cut, op->inn.hpairs);
     } else {
@@ -1115,10 +1129,12 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
         op->inn.hpairs = op->ext.hpairs;
     }
     auto t4 = now();
-    if ((s = near_build(op, op->inn, q)) != SIE_OK) return fail(s);
-    // near-only interior: approximate inverse of L_i,NR for the nested solve
-    if (!op->inn.has_grid && (s = spai_build(st, op->inn.csr, op->inn.valL, &op->inn.valM)) != SIE_OK)
-        return fail(s);
+    if (op->p.interior_model != SIE_SIBC) {
+        if ((s = near_build(op, op->inn, q)) != SIE_OK) return fail(s);
+        // near-only interior: approximate inverse of L_i,NR for the nested solve
+        if (!op->inn.has_grid && (s = spai_build(st, op->inn.csr, op->inn.valL, &op->inn.valM)) != SIE_OK)
+            return fail(s);
+    }
     op->build_ms[2] = ms(t4, now());
     // workspace
     int64_t nn = (int64_t)g.n[0] * g.n[1] * g.n[2], Ng = (int64_t)g.N[0] * g.N[1] * g.N[2];
@@ -1146,6 +1162,10 @@ sie_status sie_matvec(sie_op* op, int which, const double* x, double* y, int nrh
     if (!op || !x || !y || nrhs < 1 || which < SIE_OP_L0 || which > SIE_OP_ZI) {
         set_error("sie_matvec: invalid argument");
         return SIE_ERR_ARG;
+    }
+    if (op->p.interior_model == SIE_SIBC && (which == SIE_OP_LI || which == SIE_OP_KI)) {
+        set_error("sie_matvec: an operator built with SIE_SIBC has no interior operators");
+        return SIE_ERR_STATE;
     }
     SIE_CUDA_TRY(cudaSetDevice(op->mesh->ctx->device));
     cudaStream_t st = op->mesh->ctx->stream;
@@ -1188,6 +1208,10 @@ sie_status sie_op_near_csr(const sie_op* op, int which, int64_t* row_ptr, int32_
     if (!op || !row_ptr || !nnz || which < SIE_OP_L0 || which > SIE_OP_KI) {
         set_error("sie_op_near_csr: invalid argument");
         return SIE_ERR_ARG;
+    }
+    if (op->p.interior_model == SIE_SIBC && (which == SIE_OP_LI || which == SIE_OP_KI)) {
+        set_error("sie_op_near_csr: an operator built with SIE_SIBC has no interior operators");
+        return SIE_ERR_STATE;
     }
     const AimOp& a = (which == SIE_OP_L0 || which == SIE_OP_K0) ? op->ext : op->inn;
     int lk = (which == SIE_OP_L0 || which == SIE_OP_LI) ? 0 : 1;

@@ -441,6 +441,7 @@ void sie_params_default(sie_params* p)
     p->q_alen = 1.5;
     p->q_oratio = 0.25;
     p->dense_pc_max = 32768;
+    p->interior_model = SIE_GIBC;
 }
 
 const char* sie_last_error(void) { return g_err.c_str(); }

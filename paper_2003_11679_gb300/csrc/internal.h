@@ -264,6 +264,20 @@ struct sie_op {
     size_t gnodes[2] = {0, 0};      // nodes of the last captured graph: outside the loop, loop body
     double2* ir_buf = nullptr;      // iterative refinement: residual, correction, product (3 (ne + nt))
     double lu_ms = 0;               // wall time of the dense constraint-preconditioner factorisations
+    // surface impedance boundary condition (interior_model = SIE_SIBC): RWG Gram
+    // matrix as edge CSR, its diagonal, and eta_i / eta0
+    int64_t* gr_row_ptr = nullptr;
+    int64_t gr_nnz = 0;
+    int32_t* gr_col = nullptr;
+    double2* gr_val = nullptr;
+    double2* gr_diag = nullptr;
+    double eta_re = 0, eta_im = 0;
+    // projection of the system product as a gather: touched grid nodes, CSR
+    // of their stencil entries (t * S + u), per-triangle coefficients
+    int64_t pm_nnode = 0;
+    int64_t *pm_node = nullptr, *pm_ptr = nullptr;
+    int32_t* pm_ent = nullptr;
+    double2* pm_tc = nullptr;       // 9 per triangle (FP64; the complex64 path uses its first half)
 };
 
 // ------------------------------------------------------------------ launchers (aim.cu, near.cu)
@@ -295,6 +309,7 @@ sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int 
 // nested-solve statistics: clear them, or fold the graph's copy and return
 // SIE_ERR_NOT_CONVERGED when a nested solve ended above tol_inner
 sie_status nested_clear(sie_op* op);
+sie_status proj_map_ready(sie_op* op);
 sie_status nested_check(sie_op* op, const char* who);
 double sys_rcs_scale(const sie_op* op);
 // nbatch consecutive grids (buf + k n^3, src + k N^3) in one launch per pass

@@ -672,85 +672,89 @@ static sie_status fgmres_dev(sie_ctx* c, cudaStream_t body_st, KrylovWork& K, in
 }
 
 // ------------------------------------------------------------------ system kernels
-// grids: J from H (0..2), M from E' (3..5), charge grid from q_t = -c0rho_t (6)
-__global__ void k_project_sys(int nt, int S, int Mord, DevMesh M, const int32_t* __restrict__ base,
-                              const double* __restrict__ W, const double2* __restrict__ H,
-                              const double2* __restrict__ E, const double2* __restrict__ rho, GridDesc g,
-                              double2* __restrict__ src, int64_t Ng)
+// Projection as a gather (deterministic, no atomics): per triangle t the
+// current on t is alpha (r - c_t) + beta (alpha = sum_i c_i x_i, beta_a =
+// sum_i c_i q_ia x_i) for x = H and x = E', and the charge grid takes
+// -c0rho_t; grid node v sums, in a fixed order, the stencil entries (t, u)
+// that land on it: J_a += alpha_H w1[a] + beta_H[a] w0, M_a likewise with E',
+// rho += -c0rho_t w0.
+template <class C>
+__device__ __forceinline__ C cmk(double a, double b)
 {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nt * S) return;
-    int t = idx / S, u = idx % S;
-    const int Mp = Mord + 1;
-    int nx = base[3 * t] + u % Mp, ny = base[3 * t + 1] + (u / Mp) % Mp, nz = base[3 * t + 2] + u / (Mp * Mp);
-    int64_t node = ((int64_t)nz * g.N[1] + ny) * g.N[0] + nx;
-    const double* w = W + (size_t)idx * 4;
-    for (int f = 0; f < 2; f++) {
-        const double2* x = f ? E : H;
-        double2 al = make_double2(0, 0);
-        double2 be[3] = {al, al, al};
-        for (int i = 0; i < 3; i++) {
-            double2 xv = x[M.tri_edge[3 * t + i]];
-            double c = M.coef[3 * t + i];
-            al.x += c * xv.x;
-            al.y += c * xv.y;
-            for (int a = 0; a < 3; a++) {
-                double qq = c * M.q[9 * t + 3 * i + a];
-                be[a].x += qq * xv.x;
-                be[a].y += qq * xv.y;
-            }
-        }
-        for (int a = 0; a < 3; a++) {
-            double2* d = src + (3 * f + a) * Ng + node;
-            atomicAdd(&d->x, al.x * w[1 + a] + be[a].x * w[0]);
-            atomicAdd(&d->y, al.y * w[1 + a] + be[a].y * w[0]);
-        }
-    }
-    double2 r = rho[t];
-    double2* d = src + 6 * Ng + node;
-    atomicAdd(&d->x, -r.x * w[0]);
-    atomicAdd(&d->y, -r.y * w[0]);
+    C c;
+    c.x = a;
+    c.y = b;
+    return c;
 }
 
-// complex64 grid path (SIE_MIXED): same projection in FP32 with FP32 atomics
-__global__ void k_project_sys32(int nt, int S, int Mord, DevMesh M, const int32_t* __restrict__ base,
-                                const float* __restrict__ W, const double2* __restrict__ H,
-                                const double2* __restrict__ E, const double2* __restrict__ rho, GridDesc g,
-                                float2* __restrict__ src, int64_t Ng)
+// tc: per triangle 9 values: alpha_H, beta_H[3], alpha_E, beta_E[3], -c0rho
+template <class C>
+__global__ void k_tri_coef(int nt, DevMesh M, const double2* __restrict__ H, const double2* __restrict__ E,
+                           const double2* __restrict__ rho, C* __restrict__ tc)
 {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nt * S) return;
-    int t = idx / S, u = idx % S;
-    const int Mp = Mord + 1;
-    int nx = base[3 * t] + u % Mp, ny = base[3 * t + 1] + (u / Mp) % Mp, nz = base[3 * t + 2] + u / (Mp * Mp);
-    int64_t node = ((int64_t)nz * g.N[1] + ny) * g.N[0] + nx;
-    const float4 w = *reinterpret_cast<const float4*>(W + (size_t)idx * 4);
-    const float ww[4] = {w.x, w.y, w.z, w.w};
-    for (int f = 0; f < 2; f++) {
-        const double2* x = f ? E : H;
-        float alr = 0, ali = 0, ber[3] = {0, 0, 0}, bei[3] = {0, 0, 0};
-        for (int i = 0; i < 3; i++) {
-            double2 xv = x[M.tri_edge[3 * t + i]];
-            float c = (float)M.coef[3 * t + i];
-            float xr = (float)xv.x, xi = (float)xv.y;
-            alr += c * xr;
-            ali += c * xi;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double ar[2] = {0, 0}, ai[2] = {0, 0}, br[2][3] = {{0, 0, 0}, {0, 0, 0}}, bi[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    for (int i = 0; i < 3; i++) {
+        const int e = M.tri_edge[3 * t + i];
+        const double c = M.coef[3 * t + i];
+        const double2 xs[2] = {H[e], E[e]};
+        for (int f = 0; f < 2; f++) {
+            ar[f] += c * xs[f].x;
+            ai[f] += c * xs[f].y;
             for (int a = 0; a < 3; a++) {
-                float qq = c * (float)M.q[9 * t + 3 * i + a];
-                ber[a] += qq * xr;
-                bei[a] += qq * xi;
+                const double qq = c * M.q[9 * t + 3 * i + a];
+                br[f][a] += qq * xs[f].x;
+                bi[f][a] += qq * xs[f].y;
             }
         }
-        for (int a = 0; a < 3; a++) {
-            float2* d = src + (3 * f + a) * Ng + node;
-            atomicAdd(&d->x, alr * ww[1 + a] + ber[a] * ww[0]);
-            atomicAdd(&d->y, ali * ww[1 + a] + bei[a] * ww[0]);
-        }
     }
-    double2 r = rho[t];
-    float2* d = src + 6 * Ng + node;
-    atomicAdd(&d->x, -(float)r.x * ww[0]);
-    atomicAdd(&d->y, -(float)r.y * ww[0]);
+    C* o = tc + 9 * (int64_t)t;
+    for (int f = 0; f < 2; f++) {
+        o[4 * f] = cmk<C>(ar[f], ai[f]);
+        for (int a = 0; a < 3; a++) o[4 * f + 1 + a] = cmk<C>(br[f][a], bi[f][a]);
+    }
+    o[8] = cmk<C>(-rho[t].x, -rho[t].y);
+}
+
+// one thread per touched node; ent: t * S + u, grouped by node (ptr)
+template <class C, class R>
+__global__ void k_project_gather(int64_t nnode, const int64_t* __restrict__ node, const int64_t* __restrict__ ptr,
+                                 const int32_t* __restrict__ ent, int S, const R* __restrict__ W,
+                                 const C* __restrict__ tc, C* __restrict__ src, int64_t Ng)
+{
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nnode) return;
+    R acc[14];
+#pragma unroll
+    for (int i = 0; i < 14; i++) acc[i] = 0;
+    for (int64_t k = ptr[v]; k < ptr[v + 1]; k++) {
+        const int32_t id = ent[k];
+        const int t = id / S;
+        const R* w = W + (int64_t)id * 4;
+        const R w0 = w[0], w1[3] = {w[1], w[2], w[3]};
+        const C* c = tc + 9 * (int64_t)t;
+#pragma unroll
+        for (int f = 0; f < 2; f++) {
+            const C al = c[4 * f];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const C be = c[4 * f + 1 + a];
+                acc[2 * (3 * f + a)] += al.x * w1[a] + be.x * w0;
+                acc[2 * (3 * f + a) + 1] += al.y * w1[a] + be.y * w0;
+            }
+        }
+        acc[12] += c[8].x * w0;
+        acc[13] += c[8].y * w0;
+    }
+    const int64_t nd = node[v];
+#pragma unroll
+    for (int g = 0; g < 7; g++) {
+        C o;
+        o.x = acc[2 * g];
+        o.y = acc[2 * g + 1];
+        src[g * Ng + nd] = o;
+    }
 }
 
 __global__ void k_specmul_sys32(const float2* __restrict__ spec, float2* __restrict__ buf, int64_t nn, float k0)
@@ -1154,8 +1158,11 @@ static int inner_m(const sie_op* op) { return std::max(1, std::min(op->p.inner_m
 
 // interior impedance E' = Z' H = -(j k0 eps_r + sigma eta0)^-1 L_i^-1 (K_i - Ix/2) H
 // nested_res (stream path): relative residual the nested solve ended with
+static sie_status apply_Z_sibc(sie_op* op, const double2* H, double2* E, double* nested_res);
+
 static sie_status apply_Z(sie_op* op, const double2* H, double2* E, double* nested_res)
 {
+    if (op->p.interior_model == SIE_SIBC) return apply_Z_sibc(op, H, E, nested_res);
     sie_ctx* c = op->mesh->ctx;
     cudaStream_t st = c->stream;
     const int64_t ne = op->mesh->h.ne;
@@ -1204,6 +1211,88 @@ static sie_status apply_Z(sie_op* op, const double2* H, double2* E, double* nest
     return SIE_OK;
 }
 
+// Surface impedance boundary condition: E' = (eta_i / eta0) G^-1 Ix H, the Gram
+// system solved by the same nested FGMRES (Jacobi preconditioned; G is
+// well conditioned), on the device inside the system-product graph
+static sie_status apply_Z_sibc(sie_op* op, const double2* H, double2* E, double* nested_res)
+{
+    sie_ctx* c = op->mesh->ctx;
+    cudaStream_t st = c->stream;
+    const int64_t ne = op->mesh->h.ne;
+    double2* a = op->sys_tmp;  // ne
+    SIE_TRY(spmv(st, (int)ne, op->ix_nnz, op->ix_row_ptr, op->ix_col, op->ix_val, H, cplx(1.0, 0.0), a, false));
+    auto A = [&](const double2* x, double2* y) {
+        return spmv(c->stream, (int)ne, op->gr_nnz, op->gr_row_ptr, op->gr_col, op->gr_val, x, cplx(1.0, 0.0), y,
+                    false);
+    };
+    auto Mj = [&](const double2* x, double2* y) {
+        k_jacobi<<<nb(ne), 256, 0, c->stream>>>(ne, x, op->gr_diag, make_double2(1.0, 0.0), y);
+        SIE_CUDA_TRY(cudaGetLastError());
+        return SIE_OK;
+    };
+    const int m_in = inner_m(op);
+    if (nested_res) *nested_res = 0.0;
+    if (op->capturing) {
+        SIE_TRY(fgmres_dev(c, op->gs[1], op->kin, ne, A, Mj, a, E, op->p.tol_inner, m_in, m_in, op->gstat,
+                           &op->gnodes[1]));
+    } else {
+        int it = 0;
+        double rr = 0;
+        sie_status s;
+        {
+            Stage s_(c, "inner_solve");
+            s = fgmres(c, op->kin, ne, A, Mj, a, E, op->p.tol_inner, m_in, m_in, &it, &rr);
+        }
+        if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
+        if (nested_res) *nested_res = rr;
+        op->stats[2] = std::max(op->stats[2], (double)it);
+        op->stats[3] = std::max(op->stats[3], rr);
+    }
+    SIE_TRY(axpby(st, ne, cplx(op->eta_re, op->eta_im), E, 0.0, E));
+    return SIE_OK;
+}
+
+// node -> stencil entries map of the exterior grid (built once, on the host,
+// from the stencil bases; the operator build calls it before any capture)
+sie_status proj_map_ready(sie_op* op)
+{
+    if (op->pm_node) return SIE_OK;
+    cudaStream_t st = op->mesh->ctx->stream;
+    const GridDesc& g = op->ext.g;
+    const int Mp = g.M + 1, S = Mp * Mp * Mp;
+    const int64_t nt = op->mesh->h.nt;
+    std::vector<int32_t> hb(3 * nt);
+    SIE_CUDA_TRY(cudaMemcpyAsync(hb.data(), op->base, sizeof(int32_t) * 3 * nt, cudaMemcpyDeviceToHost, st));
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<std::pair<int64_t, int32_t>> e(nt * S);
+    for (int64_t t = 0; t < nt; t++)
+        for (int u = 0; u < S; u++) {
+            int nx = hb[3 * t] + u % Mp, ny = hb[3 * t + 1] + (u / Mp) % Mp, nz = hb[3 * t + 2] + u / (Mp * Mp);
+            e[t * S + u] = {((int64_t)nz * g.N[1] + ny) * g.N[0] + nx, (int32_t)(t * S + u)};
+        }
+    std::sort(e.begin(), e.end());
+    std::vector<int64_t> node, ptr(1, 0);
+    std::vector<int32_t> ent(e.size());
+    for (size_t k = 0; k < e.size(); k++) {
+        if (k == 0 || e[k].first != e[k - 1].first) {
+            if (k) ptr.push_back((int64_t)k);
+            node.push_back(e[k].first);
+        }
+        ent[k] = e[k].second;
+    }
+    ptr.push_back((int64_t)e.size());
+    op->pm_nnode = (int64_t)node.size();
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->pm_node, sizeof(int64_t) * node.size(), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->pm_ptr, sizeof(int64_t) * ptr.size(), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->pm_ent, sizeof(int32_t) * ent.size(), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->pm_tc, sizeof(double2) * 9 * nt, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(op->pm_node, node.data(), sizeof(int64_t) * node.size(), cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(op->pm_ptr, ptr.data(), sizeof(int64_t) * ptr.size(), cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(op->pm_ent, ent.data(), sizeof(int32_t) * ent.size(), cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIE_OK;
+}
+
 // y = SYS x, x = [H (ne); c0 rho (nt)]
 static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
 {
@@ -1228,9 +1317,12 @@ static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
         float2* buf = reinterpret_cast<float2*>(op->ws.bufs);
         {
             Stage s_(c, "project_sys32");
+            SIE_TRY(proj_map_ready(op));
             SIE_CUDA_TRY(cudaMemsetAsync(src, 0, sizeof(float2) * 7 * Ng, st));
-            k_project_sys32<<<(unsigned)((M.nt * S + 255) / 256), 256, 0, st>>>(M.nt, S, g.M, M, op->base, op->W32, H,
-                                                                                 E, rho, g, src, Ng);
+            float2* tc = reinterpret_cast<float2*>(op->pm_tc);
+            k_tri_coef<float2><<<nb(M.nt), 256, 0, st>>>(M.nt, M, H, E, rho, tc);
+            k_project_gather<float2, float><<<nb(op->pm_nnode), 256, 0, st>>>(
+                op->pm_nnode, op->pm_node, op->pm_ptr, op->pm_ent, S, op->W32, tc, src, Ng);
             SIE_CUDA_TRY(cudaGetLastError());
         }
         SIE_TRY(fft3d(st, buf, src, g, -1, 1, c, 7));
@@ -1250,9 +1342,11 @@ static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
         double2* buf = op->ws.bufs;
         {
             Stage s_(c, "project_sys");
+            SIE_TRY(proj_map_ready(op));
             SIE_CUDA_TRY(cudaMemsetAsync(src, 0, sizeof(double2) * 7 * Ng, st));
-            k_project_sys<<<(unsigned)((M.nt * S + 255) / 256), 256, 0, st>>>(M.nt, S, g.M, M, op->base, op->W, H, E,
-                                                                               rho, g, src, Ng);
+            k_tri_coef<double2><<<nb(M.nt), 256, 0, st>>>(M.nt, M, H, E, rho, op->pm_tc);
+            k_project_gather<double2, double><<<nb(op->pm_nnode), 256, 0, st>>>(
+                op->pm_nnode, op->pm_node, op->pm_ptr, op->pm_ent, S, op->W, op->pm_tc, src, Ng);
             SIE_CUDA_TRY(cudaGetLastError());
         }
         SIE_TRY(fft3d(st, buf, src, g, -1, 1, c, 7));
@@ -1530,10 +1624,77 @@ sie_status constraint_lu_check(sie_op* op)
     return SIE_OK;
 }
 
+// rows of (column, value) pairs -> device CSR (duplicate columns summed)
+static sie_status upload_rows(cudaStream_t st, std::vector<std::vector<std::pair<int32_t, double>>>& rows,
+                              int64_t** rp_d, int32_t** col_d, double2** val_d, int64_t* nnz)
+{
+    std::vector<int64_t> rp(rows.size() + 1, 0);
+    std::vector<int32_t> col;
+    std::vector<double2> val;
+    for (size_t m = 0; m < rows.size(); m++) {
+        auto& r = rows[m];
+        std::sort(r.begin(), r.end(), [](auto& a, auto& b) { return a.first < b.first; });
+        for (size_t k = 0; k < r.size(); k++) {
+            if ((int64_t)col.size() > rp[m] && col.back() == r[k].first)
+                val.back().x += r[k].second;
+            else {
+                col.push_back(r[k].first);
+                val.push_back(make_double2(r[k].second, 0.0));
+            }
+        }
+        rp[m + 1] = (int64_t)col.size();
+    }
+    *nnz = (int64_t)col.size();
+    SIE_CUDA_TRY(cudaMallocAsync((void**)rp_d, sizeof(int64_t) * rp.size(), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)col_d, sizeof(int32_t) * std::max<size_t>(col.size(), 1), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)val_d, sizeof(double2) * std::max<size_t>(val.size(), 1), st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(*rp_d, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(*col_d, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(*val_d, val.data(), sizeof(double2) * val.size(), cudaMemcpyHostToDevice, st));
+    // the host vectors must outlive the copies
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIE_OK;
+}
+
+// RWG Gram matrix G_mn = I f_m . f_n dS as edge CSR: on triangle t (centroid
+// c, I (r - c) dS = 0, I |r - c|^2 dS = A (l1^2 + l2^2 + l3^2) / 36) the block is
+// c_i c_j A [(l1^2 + l2^2 + l3^2) / 36 + (c - p_i).(c - p_j)]
+static sie_status gram_prepare(sie_op* op)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const HostMesh& h = op->mesh->h;
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(h.ne);
+    std::vector<double2> diag(h.ne, make_double2(0.0, 0.0));
+    for (int64_t t = 0; t < h.nt; t++) {
+        double l2 = 0;
+        for (int i = 0; i < 3; i++) {
+            const double* a = &h.V[3 * h.T[3 * t + i]];
+            const double* b = &h.V[3 * h.T[3 * t + (i + 1) % 3]];
+            for (int d = 0; d < 3; d++) l2 += (b[d] - a[d]) * (b[d] - a[d]);
+        }
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                const double* qi = &h.q[9 * t + 3 * i];
+                const double* qj = &h.q[9 * t + 3 * j];
+                double v = h.coef[3 * t + i] * h.coef[3 * t + j] * h.area[t] *
+                           (l2 / 36.0 + qi[0] * qj[0] + qi[1] * qj[1] + qi[2] * qj[2]);
+                rows[h.tri_edge[3 * t + i]].push_back({h.tri_edge[3 * t + j], v});
+                if (h.tri_edge[3 * t + i] == h.tri_edge[3 * t + j]) diag[h.tri_edge[3 * t + i]].x += v;
+            }
+    }
+    SIE_TRY(upload_rows(st, rows, &op->gr_row_ptr, &op->gr_col, &op->gr_val, &op->gr_nnz));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->gr_diag, sizeof(double2) * h.ne, st));
+    SIE_CUDA_TRY(cudaMemcpyAsync(op->gr_diag, diag.data(), sizeof(double2) * h.ne, cudaMemcpyHostToDevice, st));
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIE_OK;
+}
+
 sie_status sys_prepare(sie_op* op)
 {
     cudaStream_t st = op->mesh->ctx->stream;
     const HostMesh& h = op->mesh->h;
+    if (op->p.interior_model == SIE_SIBC) SIE_TRY(gram_prepare(op));
+    SIE_TRY(proj_map_ready(op));
     // Ix as an edge CSR: (Ix)_mn = I_T f_m . (n x f_n) = c_m c_n A n . ((p_n - c) x (p_m - c))
     std::vector<std::vector<std::pair<int32_t, double>>> rows(h.ne);
     for (int64_t t = 0; t < h.nt; t++) {
@@ -1608,6 +1769,9 @@ void sys_release(sie_op* op)
     op->kout.release(st);
     op->kcs_in.release(st);
     op->kcs_out.release(st);
+    for (void* p : {(void*)op->gr_row_ptr, (void*)op->gr_col, (void*)op->gr_val, (void*)op->gr_diag,
+                    (void*)op->pm_node, (void*)op->pm_ptr, (void*)op->pm_ent, (void*)op->pm_tc})
+        if (p) cudaFreeAsync(p, st);
     for (void* p : {(void*)op->ix_row_ptr, (void*)op->ix_col, (void*)op->ix_val, (void*)op->elen, (void*)op->sys_E,
                     (void*)op->sys_tmp, (void*)op->sys_vec, (void*)op->cs_e, (void*)op->cs_t, (void*)op->pc_e,
                     (void*)op->pc_t})
