@@ -206,6 +206,11 @@ sie_status sie_op_grid(const sie_op* op, double origin[3], double* h, int64_t N[
  * Eqs. (GIBCdef), (nest02), (nest2) for ZI.
  * x, y: complex128, length N_e (L0, K0, LI, KI, ZI) or N_e + N_t (SYS, the
  * AEFIE unknowns [H; c0 rho] of Eq. sys).  flags: SIE_DEVICE_PTRS or 0.
+ * L0, K0, LI and KI with nrhs > 1 run in blocks of up to 8 right-hand sides:
+ * the kernel spectra, the stencil weights and the near-region values are read
+ * once per block (one projection, FFT pass, spectral multiply, interpolation
+ * and CSR x panel launch per block).  The other operators loop over the
+ * right-hand sides.
  * SYS and ZI contain the nested solve of Eq. (nest2): one unrestarted FGMRES
  * cycle of at most min(inner_maxit, 128) iterations to tol_inner.  When it
  * ends above tol_inner, host-pointer calls return SIE_ERR_NOT_CONVERGED (y
@@ -242,7 +247,9 @@ sie_status sie_rhs_planewave(sie_op* op, const double* khat, const double* epol,
  * correction A d = r is solved with the complex64 product (as SIE_MIXED) to
  * the accuracy the sweep needs, and the sweeps stop when the FP64 residual is
  * below tol_outer (iters then counts the FGMRES iterations of all
- * corrections).  Returns SIE_ERR_NOT_CONVERGED with the last iterate in x when
+ * corrections); when a sweep does not halve the FP64 residual (the complex64
+ * product's error, amplified by cancellation, bounds what it can reach), the
+ * remaining corrections use the FP64 product.  Returns SIE_ERR_NOT_CONVERGED with the last iterate in x when
  * maxit is reached first, or when a nested interior solve of its products
  * ended above tol_inner (sie_op_stats gives both residuals). */
 sie_status sie_solve(sie_op* op, const double* b, double* x, int nrhs, int* iters, double* relres, int flags);
@@ -292,13 +299,15 @@ sie_status sie_rcs_static(sie_op* op, const double* x, const double* rhat, int n
 
 /* x = A^-1 b for one dense complex matrix with the library's GPU LU, the one
  * the constraint preconditioners use (Sec. III-D: the paper factorises its
- * preconditioner by LU): complex64 blocked LU with partial pivoting, then two
- * triangular solves, on device `device`.  A: n x n complex128 row-major
- * (host), b, x: n complex128 (host); A and b are rounded to complex64, so x
- * carries complex64 rounding amplified by the condition number.  Allocates
- * and frees its device memory; synchronises.  SIE_ERR_ARG for n < 1 or a zero
- * pivot (singular matrix). */
-sie_status sie_dense_solve(int device, int n, const double* A, const double* b, double* x);
+ * preconditioner by LU): complex64 blocked LU with partial pivoting on device
+ * `device`, then either two triangular solves (flags 0) or, as the
+ * preconditioners do, the explicit inverse U^-1 L^-1 P formed from the
+ * factors and applied as one matrix-vector product (flags 1).  A: n x n
+ * complex128 row-major (host), b, x: n complex128 (host); A is rounded to
+ * complex64, so x carries complex64 rounding amplified by the condition
+ * number.  Allocates and frees its device memory; synchronises.  SIE_ERR_ARG
+ * for n < 1 or a zero pivot (singular matrix). */
+sie_status sie_dense_solve(int device, int n, const double* A, const double* b, double* x, int flags);
 
 /* FMA throughput of device `device`: FP64 and FP32 TFLOP/s (2 flops per
  * FMA), measured by the library's own probe kernel (independent FMA chains on

@@ -210,7 +210,7 @@ class AimGIBC:
         self.zs = zscale(f, eps_r, sigma)
         if interior == "sibc":
             self._sibc = eta_medium(f, eps_r, sigma) / ETA0
-            self._lu_gram = spl.splu(sp.csc_matrix(mom.gram(mesh)))
+            self._lu_gram = spl.splu(sp.csc_matrix(mom.gram(mesh).astype(complex)))
         elif interior == "near":
             self.inn = aim.NearOnly(mesh, self.ki, cutoff, quad)
             self._lu = spl.splu(self.inn.NL.tocsc())

@@ -91,7 +91,7 @@ def lib():
         L.sie_rcs.argtypes = [P, P, P, I, P, I]
         L.sie_rcs_static.argtypes = [P, P, P, I, P, I]
         L.sie_probe_fma.argtypes = [I, P, P]
-        L.sie_dense_solve.argtypes = [I, I, P, P, P]
+        L.sie_dense_solve.argtypes = [I, I, P, P, P, I]
         for name in SYMBOLS:
             f = getattr(L, name)
             if name not in ("sie_params_default", "sie_last_error"):
@@ -112,13 +112,14 @@ def probe_fma(device=0):
     return a.value, b.value
 
 
-def dense_solve(A, b, device=0):
+def dense_solve(A, b, device=0, inverse=False):
     """x = A^-1 b with the library's GPU complex64 LU (verification of the
-    factorisation the constraint preconditioners use)."""
+    factorisation the constraint preconditioners use); inverse=True applies
+    the explicit inverse formed from the factors, as the preconditioners do."""
     A = np.ascontiguousarray(A, dtype=np.complex128)
     b = np.ascontiguousarray(b, dtype=np.complex128)
     x = np.zeros_like(b)
-    _check(lib().sie_dense_solve(device, len(b), A.ctypes.data, b.ctypes.data, x.ctypes.data))
+    _check(lib().sie_dense_solve(device, len(b), A.ctypes.data, b.ctypes.data, x.ctypes.data, 1 if inverse else 0))
     return x
 
 

@@ -1020,7 +1020,7 @@ sie_status sie_op_destroy(sie_op* op)
     sys_release(op);
     free_aim(op->ext);
     free_aim(op->inn);
-    void* ptrs[] = {op->base, op->W, op->W32, op->ws.bufs, op->ws.src, op->xtmp};
+    void* ptrs[] = {op->base, op->W, op->W32, op->ws.bufs, op->ws.src, op->xtmp, op->bws_bufs, op->bws_src, op->bws_vec};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete op;
@@ -1173,6 +1173,28 @@ sie_status sie_matvec(sie_op* op, int which, const double* x, double* y, int nrh
     const int64_t len = which == SIE_OP_SYS ? ne + nt : ne;
     bool dev = flags & SIE_DEVICE_PTRS;
     if (which >= SIE_OP_SYS) SIE_TRY(nested_clear(op));
+    if (which < SIE_OP_SYS && nrhs > 1) {
+        // blocks of up to 8 right-hand sides: spectra, weights and near values read once per block
+        AimOp& a = (which == SIE_OP_L0 || which == SIE_OP_K0) ? op->ext : op->inn;
+        const int lk = (which == SIE_OP_L0 || which == SIE_OP_LI) ? 0 : 1;
+        const int RBLK = 8;
+        if (!dev && !op->bws_vec)
+            SIE_CUDA_TRY(cudaMallocAsync((void**)&op->bws_vec, sizeof(double2) * 2 * RBLK * ne, st));
+        for (int r0 = 0; r0 < nrhs; r0 += RBLK) {
+            const int nr = std::min(RBLK, nrhs - r0);
+            const double2* X = (const double2*)x + (int64_t)r0 * ne;
+            double2* Y = (double2*)y + (int64_t)r0 * ne;
+            if (!dev) {
+                SIE_CUDA_TRY(cudaMemcpyAsync(op->bws_vec, X, sizeof(double2) * nr * ne, cudaMemcpyHostToDevice, st));
+                X = op->bws_vec;
+            }
+            double2* Yd = dev ? Y : op->bws_vec + RBLK * ne;
+            SIE_TRY(aim_apply_block(op, a, lk, X, Yd, nr));
+            if (!dev) SIE_CUDA_TRY(cudaMemcpyAsync(Y, Yd, sizeof(double2) * nr * ne, cudaMemcpyDeviceToHost, st));
+        }
+        if (!dev) SIE_CUDA_TRY(cudaStreamSynchronize(st));
+        return SIE_OK;
+    }
     for (int r = 0; r < nrhs; r++) {
         const double2* xr;
         double2* yr;

@@ -379,6 +379,52 @@ __global__ void __launch_bounds__(256) k_trsv(int n, int nblk, int dir, const fl
     publish(flags, b, epoch);
 }
 
+// Y = P: row i has its one in column perm[i] (row i of P A is row perm[i] of A)
+__global__ void k_perm_matrix(int n, const int* __restrict__ perm, float2* __restrict__ Y)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * n) return;
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    Y[idx] = make_float2(j == perm[i] ? 1.f : 0.f, 0.f);
+}
+
+// y = X b for the explicit inverse X (row-major): a warp per row, FP32
+// products, the row sum in FP64; b complex128, converted on the fly
+__global__ void __launch_bounds__(256) k_cgemv_inv(int n, const float2* __restrict__ X, const double2* __restrict__ b,
+                                                   double2* __restrict__ y)
+{
+    const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float2* row = X + (int64_t)r * n;
+    float ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+    int c = lane;
+    for (; c + 96 < n; c += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const float2 a = __ldg(row + c + 32 * u);
+            const double2 bv = __ldg(b + c + 32 * u);
+            const float br = (float)bv.x, bi = (float)bv.y;
+            ar[u] = fmaf(a.x, br, fmaf(-a.y, bi, ar[u]));
+            ai[u] = fmaf(a.x, bi, fmaf(a.y, br, ai[u]));
+        }
+    }
+    for (; c < n; c += 32) {
+        const float2 a = __ldg(row + c);
+        const double2 bv = __ldg(b + c);
+        const float br = (float)bv.x, bi = (float)bv.y;
+        ar[0] = fmaf(a.x, br, fmaf(-a.y, bi, ar[0]));
+        ai[0] = fmaf(a.x, bi, fmaf(a.y, br, ai[0]));
+    }
+    double sr = ((double)ar[0] + ar[1]) + ((double)ar[2] + ar[3]);
+    double si = ((double)ai[0] + ai[1]) + ((double)ai[2] + ai[3]);
+    for (int off = 16; off > 0; off >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, off);
+        si += __shfl_xor_sync(0xffffffffu, si, off);
+    }
+    if (lane == 0) y[r] = make_double2(sr, si);
+}
+
 __global__ void k_perm_to_f32(int n, const int* __restrict__ perm, const double2* __restrict__ b,
                               float2* __restrict__ y)
 {
@@ -398,10 +444,10 @@ __global__ void k_f32_to_f64(int n, const float2* __restrict__ a, double2* __res
 // ------------------------------------------------------------------ host side
 void DenseLU::release()
 {
-    for (void* p : {(void*)A, (void*)invL, (void*)invU, (void*)ipiv, (void*)perm, (void*)flags, (void*)counter,
-                    (void*)err, (void*)y0, (void*)y1, (void*)prow})
+    for (void* p : {(void*)A, (void*)Xinv, (void*)invL, (void*)invU, (void*)ipiv, (void*)perm, (void*)flags,
+                    (void*)counter, (void*)err, (void*)y0, (void*)y1, (void*)prow})
         if (p) cudaFree(p);
-    A = invL = invU = y0 = y1 = prow = nullptr;
+    A = Xinv = invL = invU = y0 = y1 = prow = nullptr;
     ipiv = perm = flags = counter = err = nullptr;
     n = nblk = 0;
 }
@@ -467,9 +513,46 @@ sie_status DenseLU::factor(cudaStream_t st)
     return SIE_OK;
 }
 
+// Replace the factors by the explicit inverse A^-1 = U^-1 L^-1 P (complex64):
+// Y = P, then L Y = P and U X = Y by blocked right-looking substitution, each
+// block step an in-place product with the inverted diagonal block and a GEMM
+// update of the remaining block rows.  Afterwards every solve is one
+// matrix-vector product (no dependency chain between blocks).
+sie_status DenseLU::invert(cudaStream_t st)
+{
+    float2* X = nullptr;
+    SIE_CUDA_TRY(cudaMalloc((void**)&X, sizeof(float2) * (size_t)n * n));
+    const int64_t nn = (int64_t)n * n;
+    k_perm_matrix<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(n, perm, X);
+    SIE_CUDA_TRY(cudaGetLastError());
+    for (int b = 0; b < nblk; b++) {  // L Y = P
+        const int k = b * LU_NB, kb = std::min(LU_NB, n - k);
+        float2* Yb = X + (int64_t)k * n;
+        SIE_TRY(cgemm(st, kb, n, kb, invL + (int64_t)b * LU_NB * LU_NB, LU_NB, Yb, n, Yb, n, 0));
+        const int below = n - k - kb;
+        if (below > 0) SIE_TRY(cgemm(st, below, n, kb, A + (int64_t)(k + kb) * n + k, n, Yb, n, Yb + (int64_t)kb * n, n, 1));
+    }
+    for (int b = nblk - 1; b >= 0; b--) {  // U X = Y
+        const int k = b * LU_NB, kb = std::min(LU_NB, n - k);
+        float2* Xb = X + (int64_t)k * n;
+        SIE_TRY(cgemm(st, kb, n, kb, invU + (int64_t)b * LU_NB * LU_NB, LU_NB, Xb, n, Xb, n, 0));
+        if (k > 0) SIE_TRY(cgemm(st, k, n, kb, A + k, n, Xb, n, X, n, 1));
+    }
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(A);
+    A = nullptr;
+    Xinv = X;
+    return SIE_OK;
+}
+
 // x = A^-1 b (FP64 in and out, complex64 inside)
 sie_status DenseLU::solve(cudaStream_t st, const double2* b, double2* x)
 {
+    if (Xinv) {
+        k_cgemv_inv<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, Xinv, b, x);
+        SIE_CUDA_TRY(cudaGetLastError());
+        return SIE_OK;
+    }
     epoch++;
     SIE_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int) * 2, st));
     k_perm_to_f32<<<(n + 255) / 256, 256, 0, st>>>(n, perm, b, y0);
@@ -511,7 +594,7 @@ __global__ void k_f64_to_f32(int64_t n, const double2* __restrict__ a, float2* _
     if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
-extern "C" sie_status sie_dense_solve(int device, int n, const double* A, const double* b, double* x)
+extern "C" sie_status sie_dense_solve(int device, int n, const double* A, const double* b, double* x, int flags)
 {
     using namespace sie;
     if (n < 1 || !A || !b || !x) {
@@ -545,6 +628,7 @@ extern "C" sie_status sie_dense_solve(int device, int n, const double* A, const 
     }
     k_f64_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>((int64_t)nn, dA, f.A);
     if ((s = f.factor(st)) != SIE_OK) return done(s);
+    if ((flags & 1) && (s = f.invert(st)) != SIE_OK) return done(s);
     if ((s = f.solve(st, db, dx)) != SIE_OK) return done(s);
     if ((s = f.check(st)) != SIE_OK) return done(s);
     if (cudaMemcpy(x, dx, sizeof(double2) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {

@@ -112,6 +112,7 @@ void make_quad(const sie_params& p, QuadDev& q);
 struct DenseLU {
     int n = 0, nblk = 0, epoch = 0;
     float2* A = nullptr;      // n x n row-major: the matrix, then its L and U factors
+    float2* Xinv = nullptr;   // explicit inverse (after invert(); A is freed then)
     float2* invL = nullptr;   // inverses of the unit-lower diagonal blocks (nblk x 64 x 64)
     float2* invU = nullptr;   // inverses of the upper diagonal blocks
     int* ipiv = nullptr;      // row swaps of the factorisation
@@ -123,6 +124,7 @@ struct DenseLU {
     sie_status alloc(int n_);
     void release();
     sie_status factor(cudaStream_t st);
+    sie_status invert(cudaStream_t st);
     sie_status solve(cudaStream_t st, const double2* b, double2* x);
     sie_status check(cudaStream_t st);
 };
@@ -278,6 +280,8 @@ struct sie_op {
     int64_t *pm_node = nullptr, *pm_ptr = nullptr;
     int32_t* pm_ent = nullptr;
     double2* pm_tc = nullptr;       // 9 per triangle (FP64; the complex64 path uses its first half)
+    // multi-right-hand-side block workspace (allocated on first use)
+    double2 *bws_bufs = nullptr, *bws_src = nullptr, *bws_vec = nullptr;
 };
 
 // ------------------------------------------------------------------ launchers (aim.cu, near.cu)
@@ -288,6 +292,8 @@ sie_status aim_weights(sie_op* op);
 sie_status aim_spectra(sie_op* op, AimOp& a);
 sie_status near_build(sie_op* op, AimOp& a, const QuadDev& q);
 sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, double2* y);
+// Y = A X for nr <= 8 vectors at once (spectra, weights and near values read once)
+sie_status aim_apply_block(sie_op* op, AimOp& a, int which_LK, const double2* X, double2* Y, int nr);
 sie_status aim_interp(sie_op* op, const double2* grids, int has_phi, double2 scal, double2* y);
 sie_status sys_prepare(sie_op* op);
 void sys_release(sie_op* op);

@@ -1594,6 +1594,7 @@ sie_status constraint_lu_build(sie_op* op)
         if ((s = a->lu->alloc(nt)) != SIE_OK) break;
         if ((s = dense_lu_assemble(st, *a->lu, op, *a, make_double2(kappa.real(), kappa.imag()))) != SIE_OK) break;
         if ((s = a->lu->factor(st)) != SIE_OK) break;
+        if ((s = a->lu->invert(st)) != SIE_OK) break;
     }
     if (s != SIE_OK) {
         // no room or a singular triangle system: the iterative constraint solve stays
@@ -1870,6 +1871,12 @@ sie_status sys_solve_refined(sie_op* op, const double2* b, double2* x, int* iter
     int total = 0;
     sie_status s = SIE_OK;
     const int SWEEPS = 10;
+    // the corrections run on the complex64 product while each sweep shrinks the
+    // FP64 residual by at least half; when one does not (the complex64 error,
+    // amplified by cancellation in the product, bounds what it can reach),
+    // the remaining corrections run on the FP64 product
+    bool fp64_corr = false;
+    double rel_prev = 1.0;
     for (int sweep = 0; sweep <= SWEEPS; sweep++) {
         // FP64 residual
         op->p.precision = SIE_FP64;
@@ -1884,8 +1891,10 @@ sie_status sys_solve_refined(sie_op* op, const double2* b, double2* x, int* iter
         if ((s = norm2(st, n, r, part, dot, hbuf, &rn)) != SIE_OK) break;
         rel = bn > 0 ? rn / bn : 0.0;
         if (rel < op->p.tol_outer || sweep == SWEEPS || total >= op->p.maxit) break;
+        if (sweep >= 2 && rel > 0.5 * rel_prev) fp64_corr = true;
+        rel_prev = rel;
         // correction on the complex64 product, to the accuracy this sweep needs
-        op->p.precision = SIE_MIXED;
+        op->p.precision = fp64_corr ? SIE_FP64 : SIE_MIXED;
         const double tc = std::min(1e-2, std::max(1e-6, 0.5 * op->p.tol_outer / rel));
         int it = 0;
         double rr = 0;

@@ -18,16 +18,18 @@ def _rand(n, seed):
         rng.standard_normal(n) + 1j * rng.standard_normal(n)
 
 
+@pytest.mark.parametrize("inverse", [False, True], ids=["triangular", "inverse"])
 @pytest.mark.parametrize("n", [1, 63, 64, 65, 300, 1031])
-def test_dense_solve_matches_lapack(lib, n):
+def test_dense_solve_matches_lapack(lib, n, inverse):
     A, b = _rand(n, n)
     A = A + 4.0 * np.sqrt(n) * np.eye(n)  # well conditioned
-    x = lib.dense_solve(A, b)
+    x = lib.dense_solve(A, b, inverse=inverse)
     ref = np.linalg.solve(A, b)
     assert np.linalg.norm(x - ref) <= 2e-4 * np.linalg.norm(ref)
 
 
-def test_dense_solve_needs_pivoting(lib):
+@pytest.mark.parametrize("inverse", [False, True], ids=["triangular", "inverse"])
+def test_dense_solve_needs_pivoting(lib, inverse):
     """Zero diagonal (a cyclic shift plus a small perturbation): without row
     exchanges the first pivot would be tiny."""
     n = 200
@@ -36,17 +38,18 @@ def test_dense_solve_needs_pivoting(lib):
     np.fill_diagonal(A, 0.0)
     A = A.astype(complex)
     b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
-    x = lib.dense_solve(A, b)
+    x = lib.dense_solve(A, b, inverse=inverse)
     ref = np.linalg.solve(A, b)
     assert np.linalg.norm(x - ref) <= 2e-4 * np.linalg.norm(ref)
 
 
-def test_dense_solve_large(lib):
+@pytest.mark.parametrize("inverse", [False, True], ids=["triangular", "inverse"])
+def test_dense_solve_large(lib, inverse):
     """Several panels and trailing-update tiles (n = 3000)."""
     n = 3000
     A, b = _rand(n, 11)
     A = A + 3.0 * np.sqrt(n) * np.eye(n)
-    x = lib.dense_solve(A, b)
+    x = lib.dense_solve(A, b, inverse=inverse)
     r = A @ x - b
     assert np.linalg.norm(r) <= 2e-5 * np.linalg.norm(A, 2) * np.linalg.norm(x)
 
