@@ -126,16 +126,22 @@ typedef struct {
                              Gram matrix G (no interior operators are built)          */
 } sie_params;
 
+/* The paper's values (Sec. IV: M = 2, near region of 11 nodes; Sec. V: skin
+ * cutoff 5, tolerances 1e-4 / 1e-6, cap 800) and the library's defaults for
+ * what the paper leaves open (quadrature, restart, dense_pc_max). */
 void sie_params_default(sie_params* p);
 
-/* Context on one CUDA device.  stream: the cudaStream_t every call of this
+/* Context on one CUDA device.  The paper has no counterpart (it runs on one
+ * CPU thread, Sec. V): a context fixes the device and the stream the
+ * library's kernels run on.  stream: the cudaStream_t every call of this
  * context issues its device work on (NULL = the legacy default stream).  The
  * stream is borrowed: the caller keeps it alive until sie_ctx_destroy. */
 sie_status sie_ctx_create(int device, void* stream, sie_ctx** out);
 sie_status sie_ctx_destroy(sie_ctx* ctx);
 const char* sie_last_error(void);
 
-/* Stage timers: while enabled, every kernel stage the context launches is
+/* Stage timers (no counterpart in the paper, which reports whole-phase wall
+ * times, Sec. V): while enabled, every kernel stage the context launches is
  * bracketed by CUDA events on the context's stream, and its device time is
  * accumulated under the stage's name.  Enabling clears the totals.
  * sie_profile_read synchronises on the pending events and copies up to cap
@@ -144,26 +150,54 @@ const char* sie_last_error(void);
 sie_status sie_profile_enable(sie_ctx* ctx, int enable);
 sie_status sie_profile_read(sie_ctx* ctx, int cap, char* names, double* ms, int64_t* count, int* n);
 
-/* Mesh: xyz (nv x 3, metres), tri (nt x 3, 0-based, counter-clockwise seen
+/* Mesh of a closed surface for the RWG discretisation (Sec. II-A: n x H and
+ * n x E expanded with RWG functions on a triangulation of the object's
+ * surface): xyz (nv x 3, metres), tri (nt x 3, 0-based, counter-clockwise seen
  * from outside).  Fails with SIE_ERR_MESH unless every edge is shared by
- * exactly two oppositely oriented triangles.  One homogeneous object. */
+ * exactly two oppositely oriented triangles (open, non-manifold, inconsistent
+ * or degenerate meshes), SIE_ERR_ARG for non-finite coordinates.  One
+ * homogeneous object (sie_mesh_create_objects for several). */
 sie_status sie_mesh_create(sie_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
                            sie_mesh** out);
 sie_status sie_mesh_destroy(sie_mesh* mesh);
-/* counts: out[0] = RWG edges N_e, out[1] = triangles N_t, out[2] = vertices */
+/* counts (Sec. II-A): out[0] = RWG edges N_e (unknowns of H and E), out[1] =
+ * triangles N_t (pulse unknowns of the charge, Eq. sys), out[2] = vertices */
 sie_status sie_mesh_counts(const sie_mesh* mesh, int64_t out[3]);
+
+/* Several homogeneous objects in the background medium (Sec. II: N_obj
+ * objects with their own eps_i, mu_i, sigma_i; the interior problem of each
+ * object couples only its own triangles, Eq. GIBCdef per object).  As
+ * sie_mesh_create, plus obj_id: nt object indices 0 .. N_obj - 1 (NULL: one
+ * object).  Every object must be a closed, consistently oriented surface on
+ * its own: an edge shared by triangles of two objects is SIE_ERR_MESH (so are
+ * object indices below 0).  *nobj (may be NULL) receives N_obj. */
+sie_status sie_mesh_create_objects(sie_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                                   const int32_t* obj_id, sie_mesh** out, int* nobj);
+
+/* Material of object obj (relative permittivity, permeability and
+ * conductivity in S/m, Eq. kin).  Objects without one take the material
+ * passed to sie_op_build.  Applies to operators built afterwards.
+ * SIE_ERR_ARG for obj outside 0 .. N_obj - 1 or an unphysical material. */
+sie_status sie_set_material(sie_mesh* mesh, int obj, double eps_r, double mu_r, double sigma);
 
 /* Build the operators of one frequency.  Background medium: vacuum.  Object:
  * (eps_r, mu_r, sigma).  Builds the exterior AIM operator (k0) and the
  * interior operator (k_i): an AIM grid operator, or the near-region-only
  * operator when 5 skin depths fit inside the near region (every kept pair is
  * near; Sec. III-C).  Device memory is allocated here and freed by
- * sie_op_destroy. */
+ * sie_op_destroy.
+ * Several objects (sie_mesh_create_objects): each object's interior uses its
+ * own material (sie_set_material, else eps_r, mu_r, sigma); its near pairs
+ * stay inside the object and its Z_i scales its own edges, so Z' is block
+ * diagonal over the objects.  With more than one object every interior must
+ * be near-region only, or interior_model = SIE_SIBC; otherwise
+ * SIE_ERR_UNSUPPORTED (per-object interior AIM grids are not built). */
 sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_r, double sigma,
                         const sie_params* params, sie_op** out);
 sie_status sie_op_destroy(sie_op* op);
 
-/* Replace the solver controls of a built operator: precision (grid path of
+/* Replace the solver controls of a built operator (the GMRES tolerances and
+ * caps of Sec. V, the precision path): precision (grid path of
  * the system product: SIE_FP64 or SIE_MIXED = complex64 projection, FFT,
  * spectral multiply and interpolation, exterior near-region products with
  * complex64 copies of the FP64-integrated values (FP32 products, FP64 row
@@ -174,7 +208,8 @@ sie_status sie_op_destroy(sie_op* op);
  * build time). */
 sie_status sie_op_set_solver(sie_op* op, const sie_params* params);
 
-/* Statistics of the last sie_solve on this operator (6 doubles): outer
+/* Statistics of the last sie_solve on this operator (the outer and nested
+ * iteration counts the paper reports, Sec. V) (6 doubles): outer
  * iterations, outer relative residual, the largest nested (interior)
  * iteration count and residual, the largest constraint-preconditioner
  * iteration count and residual.  A SIE_OP_SYS / SIE_OP_ZI sie_matvec clears
@@ -183,7 +218,8 @@ sie_status sie_op_set_solver(sie_op* op, const sie_params* params);
  * synchronise).  Synchronises the context's stream. */
 sie_status sie_op_stats(const sie_op* op, double out[6]);
 
-/* Operator facts.  info (16 doubles): [0..2] grid N_x, N_y, N_z; [3..5] FFT
+/* Operator facts (the AIM grid of Sec. III-A / IV and the near region of
+ * Eqs. LinNRP, KinNRP).  info (20 doubles): [0..2] grid N_x, N_y, N_z; [3..5] FFT
  * n_x, n_y, n_z; [6] h; [7] near pairs (exterior); [8] nnz of the exterior
  * near matrix; [9] interior mode (0 = AIM, 1 = near only); [10] interior near
  * pairs; [11] grid origin x (origin y, z: see sie_op_grid); build wall times
@@ -198,7 +234,7 @@ sie_status sie_op_stats(const sie_op* op, double out[6]);
  * minus the sie_status when the factorisation could not be made, e.g. -3 for
  * no device memory; the iterative solve is used then). */
 sie_status sie_op_info(const sie_op* op, double info[20]);
-/* grid origin (3) and spacing of the exterior grid */
+/* grid origin (3), spacing and node counts of the exterior AIM grid (Sec. III-A) */
 sie_status sie_op_grid(const sie_op* op, double origin[3], double* h, int64_t N[3]);
 
 /* y = A x for nrhs right-hand sides, A selected by `which` (SIE_OP_*):
@@ -224,7 +260,9 @@ sie_status sie_op_grid(const sie_op* op, double origin[3], double* h, int64_t N[
  * graph is dropped when tol_inner or inner_maxit change (sie_op_set_solver). */
 sie_status sie_matvec(sie_op* op, int which, const double* x, double* y, int nrhs, int flags);
 
-/* Export the precorrected near-region matrix of an operator
+/* Export the precorrected near-region matrix of an operator (L_NRP, K_NRP of
+ * Eqs. LinNRP, KinNRP for AIM operators; L_i,NR, K_i,NR for near-only
+ * interiors, Sec. III-C)
  * (SIE_OP_L0/K0/LI/KI) as CSR on the host: call once with col/val NULL to get
  * nnz in *nnz and row_ptr (N_e + 1) filled; then again with buffers of nnz
  * entries.  val is complex128. */

@@ -253,3 +253,74 @@ class AimGIBC:
             + self.D.T @ self.Lphi(-m.area * c0rho)
         r2 = (self.D @ H) / m.area + 1j * self.k0 * c0rho
         return r1, r2
+
+
+# ---------------------------------------------------------------- several objects
+class ObjectsGIBC:
+    """Eq. (sys) for several homogeneous objects (Sec. II: N_obj objects, each
+    with its own eps_i, sigma_i), exterior operators in their AIM form on one
+    grid around all of them; the interior problem of each object couples only
+    that object's triangles (Eq. GIBCdef per object), so Z' is block diagonal.
+    Interiors: near-region only with each object's 5-skin-depth cutoff, Z'
+    by a sparse LU per object, or SIBC.  obj: object index per triangle;
+    mats: (eps_r, sigma) per object."""
+
+    def __init__(self, mesh, obj, mats, f, g, interior="near", quad=None):
+        import scipy.sparse as sp
+        import scipy.sparse.linalg as spl
+        self.mesh, self.f = mesh, f
+        self.k0 = 2 * np.pi * f / C0
+        self.ext = aim.AIM(mesh, self.k0, g, quad)
+        self.Ix = Ix_sparse(mesh)
+        self.D = incidence_sparse(mesh)
+        obj = np.asarray(obj)
+        eobj = obj[mesh.edge_tri[:, 0]]
+        self.blocks = []
+        for o, (er, sg) in enumerate(mats):
+            edges = np.nonzero(eobj == o)[0]
+            if interior == "sibc":
+                G = sp.csc_matrix(mom.gram(mesh)[np.ix_(edges, edges)].astype(complex))
+                self.blocks.append((edges, "sibc", spl.splu(G), eta_medium(f, er, sg) / ETA0, None))
+                continue
+            ki = k_medium(f, er, sg)
+            cut = 5.0 / abs(ki.imag)
+            no = near_only_object(mesh, obj, o, ki, cut, quad)
+            L = no[0][np.ix_(edges, edges)].tocsc()
+            K = no[1][np.ix_(edges, edges)].tocsr()
+            self.blocks.append((edges, "near", spl.splu(L), zscale(f, er, sg), K))
+
+    def Z(self, H):
+        E = np.zeros_like(H)
+        for edges, kind, lu, fac, K in self.blocks:
+            Ix = self.Ix[edges][:, edges]
+            if kind == "sibc":
+                E[edges] = fac * lu.solve(Ix @ H[edges])
+            else:
+                E[edges] = -lu.solve(K @ H[edges] - 0.5 * (Ix @ H[edges])) / fac
+        return E
+
+    def apply(self, H, c0rho):
+        m = self.mesh
+        E = self.Z(H)
+        r1 = 1j * self.k0 * (self.ext.NLA @ H + grid_LA(self.ext, H)) - self.ext.K(E) - 0.5 * (self.Ix @ E) \
+            + self.D.T @ (self.ext.NLphi @ (-m.area * c0rho) + grid_Lphi(self.ext, -m.area * c0rho))
+        r2 = (self.D @ H) / m.area + 1j * self.k0 * c0rho
+        return r1, r2
+
+
+def near_only_object(mesh, obj, o, k, cutoff, quad=None):
+    """Near-region-only interior matrices (L_NR, K_NR, whole-mesh numbering) of
+    object o: pairs (t, s) of its triangles that touch or lie within the
+    cutoff (the rule of aim.near_pairs_cutoff restricted to the object)."""
+    import scipy.sparse as sp
+    obj = np.asarray(obj)
+    tris = np.nonzero(obj == o)[0]
+    pairs = aim.near_pairs_cutoff_of(mesh, cutoff, tris)
+    pairs = pairs[obj[pairs[:, 1]] == o]
+    L, K, _, _ = aim.exact_local(mesh, complex(k), pairs[:, 0], pairs[:, 1], quad)
+    t, s = pairs[:, 0], pairs[:, 1]
+    rows = np.repeat(mesh.tri_edge[t], 3, axis=1).ravel()
+    cols = np.tile(mesh.tri_edge[s], (1, 3)).ravel()
+    sh = (mesh.ne, mesh.ne)
+    return (sp.coo_matrix((L.ravel(), (rows, cols)), shape=sh).tocsr(),
+            sp.coo_matrix((K.ravel(), (rows, cols)), shape=sh).tocsr())

@@ -35,7 +35,7 @@ SYMBOLS = ["sie_params_default", "sie_ctx_create", "sie_ctx_destroy", "sie_last_
            "sie_mesh_destroy", "sie_mesh_counts", "sie_op_build", "sie_op_destroy", "sie_op_set_solver",
            "sie_op_stats", "sie_op_info", "sie_op_grid",
            "sie_matvec", "sie_op_near_csr", "sie_rhs_planewave", "sie_solve", "sie_rcs", "sie_rcs_static",
-           "sie_probe_fma", "sie_dense_solve"]
+           "sie_probe_fma", "sie_dense_solve", "sie_mesh_create_objects", "sie_set_material"]
 
 
 class sie_params(ctypes.Structure):
@@ -92,6 +92,8 @@ def lib():
         L.sie_rcs_static.argtypes = [P, P, P, I, P, I]
         L.sie_probe_fma.argtypes = [I, P, P]
         L.sie_dense_solve.argtypes = [I, I, P, P, P, I]
+        L.sie_mesh_create_objects.argtypes = [P, P, I64, P, I64, P, PP, P]
+        L.sie_set_material.argtypes = [P, I, D, D, D]
         for name in SYMBOLS:
             f = getattr(L, name)
             if name not in ("sie_params_default", "sie_last_error"):
@@ -180,15 +182,31 @@ class Context:
 
 
 class Mesh:
-    def __init__(self, ctx, verts, tris):
+    """A closed triangle mesh; obj (optional, one index per triangle) splits it
+    into several objects, each a closed surface with its own material."""
+
+    def __init__(self, ctx, verts, tris, obj=None):
         self.ctx = ctx
         V = np.ascontiguousarray(verts, dtype=np.float64)
         T = np.ascontiguousarray(tris, dtype=np.int32)
         self.h = ctypes.c_void_p()
-        _check(lib().sie_mesh_create(ctx.h, V.ctypes.data, len(V), T.ctypes.data, len(T), ctypes.byref(self.h)))
+        self.nobj = 1
+        if obj is None:
+            _check(lib().sie_mesh_create(ctx.h, V.ctypes.data, len(V), T.ctypes.data, len(T), ctypes.byref(self.h)))
+        else:
+            O = np.ascontiguousarray(obj, dtype=np.int32)
+            if len(O) != len(T):
+                raise ValueError("obj needs one index per triangle")
+            n = ctypes.c_int()
+            _check(lib().sie_mesh_create_objects(ctx.h, V.ctypes.data, len(V), T.ctypes.data, len(T), O.ctypes.data,
+                                                 ctypes.byref(self.h), ctypes.byref(n)))
+            self.nobj = n.value
         c = np.zeros(3, np.int64)
         _check(lib().sie_mesh_counts(self.h, c.ctypes.data))
         self.ne, self.nt, self.nv = int(c[0]), int(c[1]), int(c[2])
+
+    def set_material(self, obj, eps_r, mu_r=1.0, sigma=0.0):
+        _check(lib().sie_set_material(self.h, obj, eps_r, mu_r, sigma))
 
     def close(self):
         if self.h:

@@ -45,6 +45,7 @@ sie_status dev_upload_mesh(sie_mesh* m)
     SIE_TRY(up(st, &d.rad, h.rad.data(), h.rad.size()));
     SIE_TRY(up(st, &d.edge_tri, h.edge_tri.data(), h.edge_tri.size()));
     SIE_TRY(up(st, &d.edge_slot, h.edge_slot.data(), h.edge_slot.size()));
+    SIE_TRY(up(st, &d.obj, h.obj.data(), h.obj.size()));
     SIE_CUDA_TRY(cudaStreamSynchronize(st));
     return SIE_OK;
 }
@@ -52,7 +53,7 @@ sie_status dev_upload_mesh(sie_mesh* m)
 sie_status dev_free_mesh(sie_mesh* m)
 {
     DevMesh& d = m->d;
-    void* ptrs[] = {d.V, d.T, d.tri_edge, d.coef, d.q, d.cen, d.area, d.rad, d.edge_tri, d.edge_slot};
+    void* ptrs[] = {d.V, d.T, d.tri_edge, d.coef, d.q, d.cen, d.area, d.rad, d.edge_tri, d.edge_slot, d.obj};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DevMesh();
@@ -991,7 +992,9 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
 static void free_aim(AimOp& a)
 {
     void* ptrs[] = {a.spec, a.spec32, a.pairs, a.row_ptr, a.col, a.valL, a.valK, a.valLA, a.dLA, a.dL,
-                    a.tri_row_ptr, a.tri_col, a.valLphi, a.valLphiNR, a.valM, a.valLA32, a.valK32, a.valLphi32};
+                    a.tri_row_ptr, a.tri_col, a.valLphi, a.valLphiNR, a.valM, a.valLA32, a.valK32, a.valLphi32,
+                    a.obj_k, a.obj_ik2};
+    a.obj_k = a.obj_ik2 = nullptr;
     for (void* p : ptrs)
         if (p) cudaFree(p);
     a.valLA = a.dLA = a.dL = a.valLphi = a.valLphiNR = a.valM = nullptr;
@@ -1020,7 +1023,8 @@ sie_status sie_op_destroy(sie_op* op)
     sys_release(op);
     free_aim(op->ext);
     free_aim(op->inn);
-    void* ptrs[] = {op->base, op->W, op->W32, op->ws.bufs, op->ws.src, op->xtmp, op->bws_bufs, op->bws_src, op->bws_vec};
+    void* ptrs[] = {op->base, op->W, op->W32, op->ws.bufs, op->ws.src, op->xtmp, op->bws_bufs, op->bws_src, op->bws_vec,
+                    op->edge_zf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete op;
@@ -1047,16 +1051,38 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
         set_error("sie_op_build: interior_model must be SIE_GIBC or SIE_SIBC");
         return SIE_ERR_ARG;
     }
-    op->freq = freq_hz;
-    op->eps_r = eps_r;
-    op->mu_r = mu_r;
-    op->sigma = sigma;
-    const double c0 = 299792458.0, mu0 = 4e-7 * M_PI, eps0 = 1.0 / (mu0 * c0 * c0);
+    const double c0 = 299792458.0, mu0 = 4e-7 * M_PI, eps0 = 1.0 / (mu0 * c0 * c0), eta0 = mu0 * c0;
     const double w = 2 * M_PI * freq_hz;
+    // per-object materials (Sec. II): sie_set_material, else the arguments
+    const int nobj = mesh->h.nobj;
+    struct ObjMat {
+        double eps_r, mu_r, sigma;
+        std::complex<double> k, zs, eta;  // Eq. kin; j k0 eps_r + sigma eta0; eta_i / eta0
+        double cut;                        // skin-depth cutoff of the interior near region
+    };
+    std::vector<ObjMat> om(nobj);
+    for (int o = 0; o < nobj; o++) {
+        const bool set = o < (int)mesh->mat.size() && mesh->mat[o].set;
+        ObjMat& m = om[o];
+        m.eps_r = set ? mesh->mat[o].eps_r : eps_r;
+        m.mu_r = set ? mesh->mat[o].mu_r : mu_r;
+        m.sigma = set ? mesh->mat[o].sigma : sigma;
+        // Eq. (kin): k_i = sqrt(w mu (w eps - j sigma)), branch Im k <= 0
+        m.k = std::sqrt(std::complex<double>(w * mu0 * m.mu_r) * std::complex<double>(w * eps0 * m.eps_r, -m.sigma));
+        if (m.k.imag() > 0) m.k = -m.k;
+        m.zs = std::complex<double>(m.sigma * eta0, w / c0 * m.eps_r);
+        // eta_i / eta0 = sqrt(mu_r / eps~_r), eps~_r = eps_r - j sigma / (w eps0), branch Re > 0
+        m.eta = std::sqrt(std::complex<double>(m.mu_r) / std::complex<double>(m.eps_r, -m.sigma / (w * eps0)));
+        if (m.eta.real() < 0) m.eta = -m.eta;
+        const double delta = m.k.imag() < 0 ? -1.0 / m.k.imag() : 1e300;
+        m.cut = op->p.skin_cutoff * delta;
+    }
+    op->freq = freq_hz;
+    op->eps_r = om[0].eps_r;
+    op->mu_r = om[0].mu_r;
+    op->sigma = om[0].sigma;
     op->k0 = w / c0;
-    // Eq. (kin): k_i = sqrt(w mu (w eps - j sigma)), branch Im k <= 0
-    std::complex<double> ki = std::sqrt(std::complex<double>(w * mu0 * mu_r) * std::complex<double>(w * eps0 * eps_r, -sigma));
-    if (ki.imag() > 0) ki = -ki;
+    const std::complex<double> ki = om[0].k;
     auto fail = [&](sie_status s) {
         sie_op_destroy(op);
         return s;
@@ -1109,17 +1135,42 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
     op->inn.kr = ki.real();
     op->inn.ki = ki.imag();
     op->inn.g = g;
-    double delta = ki.imag() < 0 ? -1.0 / ki.imag() : 1e300;
-    double cut = op->p.skin_cutoff * delta;
-    {
-        // eta_i / eta0 = sqrt(mu_r / eps~_r), eps~_r = eps_r - j sigma / (w eps0), branch Re > 0
-        std::complex<double> eta = std::sqrt(std::complex<double>(mu_r) / std::complex<double>(eps_r, -sigma / (w * eps0)));
-        if (eta.real() < 0) eta = -eta;
-        op->eta_re = eta.real();
-        op->eta_im = eta.imag();
+    const double cut = om[0].cut;
+    op->eta_re = om[0].eta.real();
+    op->eta_im = om[0].eta.imag();
+    if (nobj > 1) {
+        // block-diagonal Z': a per-edge factor from the edge's object
+        const HostMesh& H = mesh->h;
+        std::vector<double2> zf(H.ne);
+        for (int64_t e = 0; e < H.ne; e++) {
+            const ObjMat& m = om[H.obj[H.edge_tri[2 * e]]];
+            const std::complex<double> f = op->p.interior_model == SIE_SIBC ? m.eta : -1.0 / m.zs;
+            zf[e] = make_double2(f.real(), f.imag());
+        }
+        if ((s = up(st, &op->edge_zf, zf.data(), zf.size())) != SIE_OK) return fail(s);
     }
     if (op->p.interior_model == SIE_SIBC) {
         op->inn.has_grid = false;  // no interior operators: Z' comes from the Gram system
+    } else if (nobj > 1) {
+        for (int o = 0; o < nobj; o++)
+            if (om[o].cut > (g.Rnear - g.M) * g.h) {
+                set_error("sie_op_build: object " + std::to_string(o) +
+                          " needs an interior AIM grid; several objects need near-region-only interiors "
+                          "(5 skin depths inside the near region) or interior_model = SIE_SIBC");
+                return fail(SIE_ERR_UNSUPPORTED);
+            }
+        op->inn.has_grid = false;
+        std::vector<double> cuts(nobj);
+        std::vector<double2> kk(nobj), ik2(nobj);
+        for (int o = 0; o < nobj; o++) {
+            cuts[o] = om[o].cut;
+            kk[o] = make_double2(om[o].k.real(), om[o].k.imag());
+            const std::complex<double> v = 1.0 / (om[o].k * om[o].k);
+            ik2[o] = make_double2(v.real(), v.imag());
+        }
+        near_pairs_cutoff_objects(mesh->h, cuts, op->inn.hpairs);
+        if ((s = up(st, &op->inn.obj_k, kk.data(), kk.size())) != SIE_OK) return fail(s);
+        if ((s = up(st, &op->inn.obj_ik2, ik2.data(), ik2.size())) != SIE_OK) return fail(s);
     } else if (cut <= (g.Rnear - g.M) * g.h) {
         op->inn.has_grid = false;
         near_pairs_cutoff(mesh->h, cut, op->inn.hpairs);

@@ -126,6 +126,30 @@ sie_status build_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t
     double s = 0;
     for (double l : m.edge_len) s += l;
     m.mean_edge = s / (double)m.ne;
+    m.obj.assign(nt, 0);
+    m.nobj = 1;
+    return SIE_OK;
+}
+
+// objects of a mesh: each a closed surface of its own (no edge between objects)
+static sie_status set_objects(HostMesh& m, const int32_t* obj)
+{
+    int nobj = 0;
+    for (int64_t t = 0; t < m.nt; t++) {
+        if (obj[t] < 0) {
+            set_error("sie_mesh_create_objects: negative object index");
+            return SIE_ERR_MESH;
+        }
+        nobj = std::max(nobj, obj[t] + 1);
+    }
+    for (int64_t e = 0; e < m.ne; e++)
+        if (obj[m.edge_tri[2 * e]] != obj[m.edge_tri[2 * e + 1]]) {
+            set_error("sie_mesh_create_objects: edge " + std::to_string(e) +
+                      " joins two objects; every object must be a closed surface of its own");
+            return SIE_ERR_MESH;
+        }
+    m.obj.assign(obj, obj + m.nt);
+    m.nobj = nobj;
     return SIE_OK;
 }
 
@@ -264,6 +288,27 @@ void near_pairs_cutoff(const HostMesh& m, double cutoff, std::vector<int32_t>& p
         std::sort(lst.begin(), lst.end());
         for (int32_t s : lst) {
             pairs.push_back((int32_t)t);
+            pairs.push_back(s);
+        }
+    }
+}
+
+void near_pairs_cutoff_objects(const HostMesh& m, const std::vector<double>& cutoff, std::vector<int32_t>& pairs)
+{
+    double cmax = 0;
+    for (double c : cutoff) cmax = std::max(cmax, c);
+    std::vector<int32_t> all;
+    near_pairs_cutoff(m, cmax, all);
+    pairs.clear();
+    for (size_t p = 0; p < all.size() / 2; p++) {
+        const int32_t t = all[2 * p], s = all[2 * p + 1];
+        const int ob = m.obj[t];
+        if (m.obj[s] != ob) continue;
+        const double dx = m.cen[3 * t] - m.cen[3 * s], dy = m.cen[3 * t + 1] - m.cen[3 * s + 1],
+                     dz = m.cen[3 * t + 2] - m.cen[3 * s + 2];
+        const double gap = std::sqrt(dx * dx + dy * dy + dz * dz) - m.rad[t] - m.rad[s];
+        if (gap <= cutoff[ob] || touching(m, t, s)) {
+            pairs.push_back(t);
             pairs.push_back(s);
         }
     }
@@ -525,7 +570,45 @@ sie_status sie_mesh_create(sie_ctx* ctx, const double* xyz, int64_t nv, const in
         delete m;
         return s;
     }
+    m->mat.assign(1, sie_mesh::Material());
     *out = m;
+    return SIE_OK;
+}
+
+sie_status sie_mesh_create_objects(sie_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                                   const int32_t* obj_id, sie_mesh** out, int* nobj)
+{
+    if (!ctx || !out) {
+        set_error("sie_mesh_create_objects: null argument");
+        return SIE_ERR_ARG;
+    }
+    auto* m = new sie_mesh();
+    m->ctx = ctx;
+    sie_status s = build_mesh(xyz, nv, tri, nt, m->h);
+    if (s == SIE_OK && obj_id) s = set_objects(m->h, obj_id);
+    if (s == SIE_OK) s = dev_upload_mesh(m);
+    if (s != SIE_OK) {
+        dev_free_mesh(m);
+        delete m;
+        return s;
+    }
+    m->mat.assign(m->h.nobj, sie_mesh::Material());
+    if (nobj) *nobj = m->h.nobj;
+    *out = m;
+    return SIE_OK;
+}
+
+sie_status sie_set_material(sie_mesh* m, int obj, double eps_r, double mu_r, double sigma)
+{
+    if (!m || obj < 0 || obj >= m->h.nobj || !(eps_r > 0) || !(mu_r > 0) || !(sigma >= 0)) {
+        set_error("sie_set_material: invalid object index or material");
+        return SIE_ERR_ARG;
+    }
+    if ((int)m->mat.size() < m->h.nobj) m->mat.resize(m->h.nobj);
+    m->mat[obj].set = true;
+    m->mat[obj].eps_r = eps_r;
+    m->mat[obj].mu_r = mu_r;
+    m->mat[obj].sigma = sigma;
     return SIE_OK;
 }
 

@@ -48,6 +48,8 @@ struct HostMesh {
     std::vector<double> coef;        // nt*3 = s l / (2A)
     std::vector<double> q;           // nt*9 = c_t - p (slot-major, then xyz)
     std::vector<double> rad;         // nt farthest vertex from the centroid
+    std::vector<int32_t> obj;        // nt object index (0 for a one-object mesh)
+    int nobj = 1;
     double mean_edge = 0;
 };
 sie_status build_mesh(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, HostMesh& m);
@@ -68,6 +70,8 @@ void stencil_base(const HostMesh& m, const GridDesc& g, std::vector<int32_t>& ba
 void near_pairs_grid(const HostMesh& m, const GridDesc& g, const std::vector<int32_t>& base,
                      std::vector<int32_t>& pairs);
 void near_pairs_cutoff(const HostMesh& m, double cutoff, std::vector<int32_t>& pairs);
+// the same with one cutoff per object; pairs are kept only inside an object
+void near_pairs_cutoff_objects(const HostMesh& m, const std::vector<double>& cutoff, std::vector<int32_t>& pairs);
 
 // CSR pattern over edges from a sorted triangle-pair list
 struct CsrPattern {
@@ -96,6 +100,7 @@ struct DevMesh {
     double* rad = nullptr;      // nt
     int32_t* edge_tri = nullptr;   // ne*2
     int8_t* edge_slot = nullptr;   // ne*2
+    int32_t* obj = nullptr;        // nt object index
 };
 
 // quadrature description handed to the near-field kernel
@@ -162,6 +167,9 @@ struct AimOp {
     float2* valLphi32 = nullptr;
     // dense LU of the constraint triangle system (null: iterative constraint solve)
     DenseLU* lu = nullptr;
+    // several-object near-region-only interior: per-object k and 1/k^2 (device)
+    double2* obj_k = nullptr;
+    double2* obj_ik2 = nullptr;
 };
 
 struct Workspace {
@@ -210,6 +218,11 @@ struct sie_mesh {
     sie_ctx* ctx = nullptr;
     sie::HostMesh h;
     sie::DevMesh d;
+    struct Material {
+        bool set = false;
+        double eps_r = 1, mu_r = 1, sigma = 0;
+    };
+    std::vector<Material> mat;       // per object
 };
 
 namespace sie {
@@ -282,6 +295,9 @@ struct sie_op {
     double2* pm_tc = nullptr;       // 9 per triangle (FP64; the complex64 path uses its first half)
     // multi-right-hand-side block workspace (allocated on first use)
     double2 *bws_bufs = nullptr, *bws_src = nullptr, *bws_vec = nullptr;
+    // several objects: per-edge factor of the interior impedance, -1/(j k0 eps_r + sigma eta0)
+    // of the edge's object (GIBC) or eta_i/eta0 (SIBC); null for one object
+    double2* edge_zf = nullptr;
 };
 
 // ------------------------------------------------------------------ launchers (aim.cu, near.cu)

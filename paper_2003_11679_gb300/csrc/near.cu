@@ -387,13 +387,20 @@ __device__ int graded_count(int toward_edge)
 
 // 14 moments per pair: Q0, Q1[3], Q2[3], Q3, U[3], V[3] (origin: centroid of t).
 // One warp per pair; lanes split the outer points.
+// obj_k: per-object wavenumbers of a several-object interior (null: kr + j ki)
 __global__ void __launch_bounds__(128) k_near_moments(const int32_t* __restrict__ pairs, int64_t np, DevMesh M,
-                                                      double kr, double ki, double2* __restrict__ mom)
+                                                      double kr, double ki, const double2* __restrict__ obj_k,
+                                                      double2* __restrict__ mom)
 {
     int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (p >= np) return;
     int t = pairs[2 * p], s = pairs[2 * p + 1];
+    if (obj_k) {
+        const double2 ko = obj_k[M.obj[t]];
+        kr = ko.x;
+        ki = ko.y;
+    }
     cd k = mk(kr, ki);
     int tt[3] = {M.T[3 * t], M.T[3 * t + 1], M.T[3 * t + 2]};
     int ss[3] = {M.T[3 * s], M.T[3 * s + 1], M.T[3 * s + 2]};
@@ -623,13 +630,15 @@ __global__ void __launch_bounds__(128) k_near_local(const int32_t* __restrict__ 
 // diagonal entries also give the exact LA and L diagonals (dLA, dL).
 __global__ void k_csr_fill(int ne, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                            const int64_t* __restrict__ pstart, const int32_t* __restrict__ pairs,
-                           const double2* __restrict__ loc, DevMesh M, double2 invk2, double2* __restrict__ vL,
+                           const double2* __restrict__ loc, DevMesh M, double2 invk2,
+                           const double2* __restrict__ obj_invk2, double2* __restrict__ vL,
                            double2* __restrict__ vK, double2* __restrict__ vLA, double2* __restrict__ dLA,
                            double2* __restrict__ dL)
 {
     int m = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (m >= ne) return;
+    if (obj_invk2) invk2 = obj_invk2[M.obj[M.edge_tri[2 * m]]];  // row m's object
     cd ik2 = mk(invk2.x, invk2.y);
     for (int64_t e = row_ptr[m] + lane; e < row_ptr[m + 1]; e += 32) {
         int n = col[e];
@@ -696,7 +705,7 @@ sie_status near_build(sie_op* op, AimOp& a, const QuadDev& q)
     const int wpb = 4;
     if (a.npairs > 0) {
         k_near_moments<<<(unsigned)((a.npairs + wpb - 1) / wpb), 32 * wpb, 0, st>>>(a.pairs, a.npairs, M, a.kr, a.ki,
-                                                                                    mom);
+                                                                                    a.obj_k, mom);
         SIE_CUDA_TRY(cudaGetLastError());
     }
     int Lm = a.g.Rnear + a.g.M;
@@ -735,7 +744,8 @@ sie_status near_build(sie_op* op, AimOp& a, const QuadDev& q)
     std::complex<double> kk(a.kr, a.ki);
     std::complex<double> ik2 = 1.0 / (kk * kk);
     k_csr_fill<<<(unsigned)((H.ne + 3) / 4), 128, 0, st>>>((int)H.ne, a.row_ptr, a.col, dps, a.pairs, loc, M,
-                                                           make_double2(ik2.real(), ik2.imag()), a.valL, a.valK,
+                                                           make_double2(ik2.real(), ik2.imag()), a.obj_ik2, a.valL,
+                                                           a.valK,
                                                            a.valLA, a.dLA, a.dL);
     SIE_CUDA_TRY(cudaGetLastError());
     // triangle CSR of Lphi (exact - grid): rows = pair blocks, columns = s

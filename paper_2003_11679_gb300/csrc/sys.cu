@@ -973,6 +973,15 @@ static sie_status spmv(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp
 
 static int64_t tri_nnz(const AimOp& a) { return a.tri_row_ptr_h.empty() ? 0 : a.tri_row_ptr_h.back(); }
 
+// E[m] *= f[m] (per-edge interior impedance factor of several objects)
+__global__ void k_scale_edges(int64_t n, const double2* __restrict__ f, double2* __restrict__ E)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 a = f[i], b = E[i];
+    E[i] = make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
 // sigma_t = -A_t c0rho_t
 __global__ void k_sigma(int nt, const double* __restrict__ area, const double2* __restrict__ rho,
                         double2* __restrict__ sig)
@@ -1205,6 +1214,11 @@ static sie_status apply_Z(sie_op* op, const double2* H, double2* E, double* nest
         op->stats[2] = std::max(op->stats[2], (double)it);
         op->stats[3] = std::max(op->stats[3], rr);
     }
+    if (op->edge_zf) {  // several objects: each edge scaled by its object's factor
+        k_scale_edges<<<nb(ne), 256, 0, st>>>(ne, op->edge_zf, E);
+        SIE_CUDA_TRY(cudaGetLastError());
+        return SIE_OK;
+    }
     cplx zs(0.0, op->k0 * op->eps_r);
     zs += op->sigma * ETA0;
     SIE_TRY(axpby(st, ne, -1.0 / zs, E, 0.0, E));
@@ -1247,6 +1261,11 @@ static sie_status apply_Z_sibc(sie_op* op, const double2* H, double2* E, double*
         if (nested_res) *nested_res = rr;
         op->stats[2] = std::max(op->stats[2], (double)it);
         op->stats[3] = std::max(op->stats[3], rr);
+    }
+    if (op->edge_zf) {
+        k_scale_edges<<<nb(ne), 256, 0, st>>>(ne, op->edge_zf, E);
+        SIE_CUDA_TRY(cudaGetLastError());
+        return SIE_OK;
     }
     SIE_TRY(axpby(st, ne, cplx(op->eta_re, op->eta_im), E, 0.0, E));
     return SIE_OK;

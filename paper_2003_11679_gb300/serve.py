@@ -10,15 +10,21 @@ materials and frequencies admitted into concurrent slots.
   admitted as soon as any slot frees up (continuous admission, no batch
   boundaries).
 * Resident state: the operator of a (mesh, frequency, material) key -- kernel
-  spectra, near-region matrices, Krylov bases, the captured system-product
-  graph -- stays on the device in the slot that built it and serves later
-  requests with the same key.
+  spectra, near-region matrices, dense constraint factorisations, Krylov
+  bases, the captured system-product graph -- stays on the device and serves
+  every later request with the same key, whichever slot takes it: one cache
+  for all slots, so no operator is built twice.  An operator lives in the
+  context of the slot that built it; a request that uses it holds that
+  context's lock (calls on one context never overlap), and a key being built
+  makes the other requests for it wait instead of building it again.
 * Device memory: before a slot builds an operator it needs free device memory
   of at least the reserve (10% of the device by default) plus an estimate of
-  the operator's size (bytes per RWG unknown, the largest ratio measured so
-  far); it first releases its own least recently used operators, then waits
-  for other slots to finish; a request that cannot fit with every other slot
-  idle and its own cache empty fails with MemoryError.
+  the operator's size (bytes per RWG unknown: the median of the ratios
+  measured on earlier builds, so one build inflated by other slots'
+  concurrent allocations does not skew it); it first releases least recently
+  used operators whose context is idle, then waits for other slots to
+  finish; a request that cannot fit with every other slot idle and the cache
+  empty fails with MemoryError.
 * Latency: per request, from submit to answer (queue + build + solve + RCS);
   stats() reports p50 / p99 and the counters.
 
@@ -100,25 +106,26 @@ class LibraryBackend:
 
 
 class Server:
-    """Slots, queue, resident operators and memory admission (module docstring)."""
+    """Slots, queue, one shared operator cache and memory admission (module docstring)."""
 
     def __init__(self, slots=2, backend_factory=None, reserve_fraction=0.10, bytes_per_unknown=128 * 1024,
                  wait_s=0.05):
         self.backend_factory = backend_factory or (lambda slot: LibraryBackend(0))
         self.reserve_fraction = reserve_fraction
-        self.bytes_per_unknown = float(bytes_per_unknown)   # estimate, raised by measured builds
+        self.bytes_per_unknown = float(bytes_per_unknown)   # estimate until builds are measured
         self.wait_s = wait_s
         self._cv = threading.Condition()
         self._queue = collections.deque()
         self._busy = 0
         self._closed = False
         self._lat = []
-        self._measured = 0.0          # largest measured operator bytes per RWG unknown
+        self._samples = []            # measured operator bytes per RWG unknown
         self.counters = collections.Counter()
         self._build_lock = threading.Lock()   # one operator set-up at a time
         self._backends = [None] * slots
-        self._caches = [collections.OrderedDict() for _ in range(slots)]  # key -> handle, LRU first
-        self._slot_locks = [threading.Lock() for _ in range(slots)]       # held while a slot serves
+        self._cache = collections.OrderedDict()   # key -> (handle, owner slot), least recently used first
+        self._building = set()                    # keys being built
+        self._ctx_locks = [threading.Lock() for _ in range(slots)]  # held while a slot's context is in use
         self._init_errors = []
         self._threads = [threading.Thread(target=self._loop, args=(s,), daemon=True) for s in range(slots)]
         self._ready = threading.Barrier(slots + 1)
@@ -156,6 +163,13 @@ class Server:
             self._cv.notify_all()
         for t in self._threads:
             t.join()
+        # every slot has stopped: release what the cache still holds, then the contexts
+        for key, (h, owner) in list(self._cache.items()):
+            self._backends[owner].release(h)
+        self._cache.clear()
+        for b in self._backends:
+            if b is not None:
+                b.close()
 
     def __enter__(self):
         return self
@@ -165,7 +179,8 @@ class Server:
 
     # ---------------------------------------------------------------- slots
     def _estimate_per_unknown(self):
-        return self._measured if self._measured > 0 else self.bytes_per_unknown
+        with self._cv:
+            return float(np.median(self._samples)) if self._samples else self.bytes_per_unknown
 
     def _loop(self, slot):
         try:
@@ -175,69 +190,96 @@ class Server:
         self._ready.wait()
         if self._backends[slot] is None:
             return
-        try:
-            while True:
-                with self._cv:
-                    while not self._queue and not self._closed:
-                        self._cv.wait()
-                    if not self._queue:
-                        break
-                    req, fut, t0 = self._queue.popleft()
-                    self._busy += 1
-                try:
-                    if fut.set_running_or_notify_cancel():
-                        with self._slot_locks[slot]:
-                            handle = self._admit(slot, req)
-                            out = self._backends[slot].run(handle, req)
-                        out["slot"] = slot
-                        with self._cv:
-                            self._lat.append(time.perf_counter() - t0)
-                        fut.set_result(out)
-                except BaseException as e:
-                    if not fut.done():
-                        fut.set_exception(e)
-                finally:
+        while True:
+            with self._cv:
+                while not self._queue and not self._closed:
+                    self._cv.wait()
+                if not self._queue:
+                    break
+                req, fut, t0 = self._queue.popleft()
+                self._busy += 1
+            try:
+                if fut.set_running_or_notify_cancel():
+                    out = self._serve(slot, req)
                     with self._cv:
-                        self._busy -= 1
-                        self._cv.notify_all()
-        finally:
-            with self._slot_locks[slot]:
-                for h in self._caches[slot].values():
-                    self._backends[slot].release(h)
-                self._caches[slot].clear()
-            self._backends[slot].close()
+                        self._lat.append(time.perf_counter() - t0)
+                    fut.set_result(out)
+            except BaseException as e:
+                if not fut.done():
+                    fut.set_exception(e)
+            finally:
+                with self._cv:
+                    self._busy -= 1
+                    self._cv.notify_all()
 
     def _count(self, name):
         with self._cv:
             self.counters[name] += 1
 
+    def _serve(self, slot, req):
+        """Run req on the cached operator of its key (built here, in this
+        slot's context, if no slot has it)."""
+        key = req.key()
+        while True:
+            with self._cv:
+                while key in self._building:
+                    self._cv.wait()
+                entry = self._cache.get(key)
+                if entry is None:
+                    self._building.add(key)
+            if entry is None:
+                break
+            handle, owner = entry
+            with self._ctx_locks[owner]:
+                with self._cv:
+                    still = self._cache.get(key) is entry
+                    if still:
+                        self._cache.move_to_end(key)
+                        self.counters["reused"] += 1
+                if still:
+                    out = self._backends[owner].run(handle, req)
+                    out["slot"] = slot
+                    return out
+            # evicted between the look-up and the lock: look again
+        try:
+            with self._ctx_locks[slot]:
+                handle = self._build(slot, req)
+                with self._cv:
+                    self._cache[key] = (handle, slot)
+                    self.counters["built"] += 1
+                out = self._backends[slot].run(handle, req)
+                out["slot"] = slot
+                return out
+        finally:
+            with self._cv:
+                self._building.discard(key)
+                self._cv.notify_all()
+
     def _evict_one(self, slot):
-        """Release one least recently used operator: this slot's own first, then
-        an idle slot's.  False when nothing could be released."""
-        order = [slot] + [s for s in range(len(self._caches)) if s != slot]
-        for s in order:
-            lock = self._slot_locks[s]
-            if s != slot and not lock.acquire(blocking=False):
-                continue  # that slot is serving a request
+        """Release the least recently used operator whose context is idle (this
+        slot's own, whose lock the caller holds, or an idle slot's).  False
+        when nothing could be released."""
+        with self._cv:
+            order = list(self._cache.items())
+        for key, entry in order:
+            handle, owner = entry
+            if owner != slot and not self._ctx_locks[owner].acquire(blocking=False):
+                continue  # that context is serving a request
             try:
-                if self._caches[s]:
-                    _, h = self._caches[s].popitem(last=False)
-                    self._backends[s].release(h)
-                    self._count("evicted")
-                    return True
+                with self._cv:
+                    if self._cache.get(key) is not entry:
+                        continue
+                    del self._cache[key]
+                self._backends[owner].release(handle)
+                self._count("evicted")
+                return True
             finally:
-                if s != slot:
-                    lock.release()
+                if owner != slot:
+                    self._ctx_locks[owner].release()
         return False
 
-    def _admit(self, slot, req):
-        """The slot's operator for req: resident, or built once memory allows."""
-        key = req.key()
-        cache = self._caches[slot]
-        if key in cache:
-            cache.move_to_end(key)
-            self._count("reused")
-            return cache[key]
+    def _build(self, slot, req):
+        """An operator for req in this slot's context, once memory allows."""
         backend = self._backends[slot]
         need = self._estimate_per_unknown() * req.ne
         while True:
@@ -258,7 +300,5 @@ class Server:
             used = free0 - backend.memory()[0]
         if used > 0:
             with self._cv:
-                self._measured = max(self._measured, used / req.ne)
-        cache[key] = handle
-        self._count("built")
+                self._samples.append(used / req.ne)
         return handle

@@ -50,7 +50,11 @@ def test_block_products_device_pointers(lib, diel):
     op.matvec(lib.SIE_OP_K0, Xd, Yd, nrhs=8)
     torch.cuda.synchronize()
     Yh = op.matvec(lib.SIE_OP_K0, X, nrhs=8)
-    assert np.array_equal(Yd.cpu().numpy(), Yh)
+    # the block projection scatters with atomics: the summation order of a grid
+    # node's contributions differs between runs, each ~1e-16 relative
+    Yd = Yd.cpu().numpy()
+    for r in range(8):
+        assert np.linalg.norm(Yd[r] - Yh[r]) <= 1e-13 * np.linalg.norm(Yh[r])
 
 
 def test_block_products_near_only(lib, ctx):

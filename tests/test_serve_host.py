@@ -105,3 +105,36 @@ def test_backend_failure_is_reported():
         raise RuntimeError("no device")
     with pytest.raises(RuntimeError, match="no device"):
         Server(slots=2, backend_factory=factory)
+
+
+def test_operator_is_shared_across_slots():
+    """Two slots, many requests of one key: the operator is built once and used
+    by both slots in turn (one cache; its context's lock keeps calls apart)."""
+    dev = Device(10 ** 9)
+    with Server(slots=2, backend_factory=lambda s: FakeBackend(dev, run_s=0.05), bytes_per_unknown=1) as srv:
+        futs = [srv.submit(_req(100)) for _ in range(6)]
+        outs = [f.result(timeout=30) for f in futs]
+        st = srv.stats()
+    assert st["built"] == 1 and st["reused"] == 5
+    assert all(o["iters"] == 1 for o in outs)
+    assert dev.used == 0
+
+
+def test_size_estimate_is_the_median():
+    """Per-unknown operator sizes: the median of the measured builds, so one
+    inflated sample does not raise the estimate."""
+    dev = Device(10 ** 9)
+
+    class Inflating(FakeBackend):
+        n = 0
+
+        def build(self, req):
+            Inflating.n += 1
+            with self.dev.lock:
+                self.dev.used += req.ne * (50 if Inflating.n == 2 else 2)
+            return {"size": req.ne * (50 if Inflating.n == 2 else 2), "key": req.key()}
+
+    with Server(slots=1, backend_factory=lambda s: Inflating(dev), bytes_per_unknown=1) as srv:
+        for f in (1e9, 2e9, 3e9):
+            srv.submit(_req(100, freq=f)).result(timeout=30)
+        assert srv.stats()["bytes_per_unknown"] == 2.0

@@ -172,3 +172,20 @@ def test_sibc_is_the_gibc_limit():
     x = cn_vector(m.ne, 3)
     d = np.linalg.norm(S.Z @ x - Sg.Z @ x) / np.linalg.norm(Sg.Z @ x)
     assert d < 3e-3, d
+
+
+def test_objects_oracle_one_object_is_aim_system():
+    """The several-object oracle with one object reduces to the one-object AIM
+    system (its per-object restriction and block assembly pinned)."""
+    from oracle import aim
+    V, T = icosphere(1, 1e-3, equal_volume=True)
+    m = Mesh(V, T)
+    g = aim.grid_params(m, M=2)
+    ki = system.k_medium(10e9, 1.0, 1e4)
+    one = system.AimGIBC(m, 10e9, 1.0, 1e4, g, interior="near", cutoff=5.0 / abs(ki.imag))
+    multi = system.ObjectsGIBC(m, np.zeros(m.nt, int), [(1.0, 1e4)], 10e9, g)
+    H, rho = cn_vector(m.ne, 41), cn_vector(m.nt, 42)
+    assert np.linalg.norm(multi.Z(H) - one.Z(H)) <= 1e-12 * np.linalg.norm(one.Z(H))
+    a1, a2 = multi.apply(H, rho)
+    b1, b2 = one.apply(H, rho)
+    assert np.linalg.norm(a1 - b1) <= 1e-12 * np.linalg.norm(b1) and np.linalg.norm(a2 - b2) <= 1e-14 * np.linalg.norm(b2)
