@@ -277,7 +277,14 @@ sie_status sie_rhs_planewave(sie_op* op, const double* khat, const double* epol,
 
 /* Solve SYS x = b (Eq. sys) by restarted FGMRES (FP64 Arnoldi, right
  * preconditioned by the AEFIE constraint preconditioner, zero initial guess)
- * until the true relative residual is below tol_outer.  b, x: complex128,
+ * until the true relative residual is below tol_outer.  The residual is
+ * measured with the charge rows of Eq. (sys) weighted by
+ * q_w = mean_m |L_A,mm|, which gives the two diagonal blocks of the
+ * constraint preconditioner (j k0 diag(L_A) and j k0 I) the same size:
+ * relres = |W (b - A x)| / |W b|, W = diag(I, q_w I).  Unweighted, the
+ * charge rows (a divergence per triangle, ~1e16 times a Galerkin potential
+ * entry on a finely meshed millimetre object) make the FP64 rounding of
+ * F D H + j k0 c0 rho alone reach 1e-3 of |b|.  b, x: complex128,
  * N_e + N_t per right-hand side ([H; c0 rho]), nrhs consecutive vectors.
  * iters / relres: per rhs (host arrays of nrhs, may be NULL).
  * flags: SIE_DEVICE_PTRS; SIE_SOLVE_REFINE = mixed-precision iterative

@@ -15,6 +15,7 @@
 
 #include "internal.h"
 #include "spmv.cuh"
+#include "sysmul.cuh"
 
 namespace sie {
 
@@ -120,6 +121,22 @@ static sie_status to_c64(cudaStream_t st, const double2* a, int64_t n, float2** 
 {
     SIE_CUDA_TRY(cudaMallocAsync((void**)out, sizeof(float2) * std::max<int64_t>(n, 1), st));
     if (n > 0) k_to_f32<<<(unsigned)((2 * n + 255) / 256), 256, 0, st>>>((const double*)a, (float*)*out, 2 * n);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+// out[e] = (a[e], b[e]) in complex64: two matrices of one pattern interleaved
+__global__ void k_to_c64_pair(const double2* __restrict__ a, const double2* __restrict__ b, float4* __restrict__ out,
+                              int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float4((float)a[i].x, (float)a[i].y, (float)b[i].x, (float)b[i].y);
+}
+
+static sie_status to_c64_pair(cudaStream_t st, const double2* a, const double2* b, int64_t n, float4** out)
+{
+    SIE_CUDA_TRY(cudaMallocAsync((void**)out, sizeof(float4) * std::max<int64_t>(n, 1), st));
+    if (n > 0) k_to_c64_pair<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, *out, n);
     SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
 }
@@ -607,6 +624,183 @@ static sie_status launch_stockham(cudaStream_t st, const C* in, C* out, int inv,
     return SIE_OK;
 }
 
+// ------------------------------------------------------------------ fused z stage of the system product
+// Forward z-transforms of the seven source grids, the spectral products of
+// Eq. (sys) (sys_specmul) and the inverse z-transforms of the four result
+// grids, PB (x, y) columns per CTA: the full-length z spectra of a column
+// stay in shared memory, so the 7 + 4 grids of n^3 are neither written out by
+// the forward z pass nor read back by the spectral multiply and the inverse z
+// pass.  Reads z < nz_phys of the seven grids, writes z < nz_phys of grids
+// 0..3 (the inverse y pass reads nothing else).  Thread layout: grid g (7),
+// then pencil-fastest within the grid (coalesced rows along x).  Shared
+// memory: two pitch-(n + 1) arrays per (grid, pencil), the spectrum A and one
+// Stockham ping-pong buffer T; the passes alternate so that the forward chain
+// ends in A and the inverse chain starts from it.
+template <int LOGN, int PB, class C, class R>
+__global__ void __launch_bounds__(7 * PB * (1 << LOGN) / 8)
+    k_fft_z_sys(C* __restrict__ buf, const C* __restrict__ spec, const C* __restrict__ tw, int nz_phys,
+                int64_t ncol, int64_t plane, int64_t bnn, R k0)
+{
+    constexpr int n = 1 << LOGN;
+    constexpr int TPP = n / 8;
+    constexpr int pitch = n + 1;
+    constexpr int NP8 = LOGN / 3, REM = LOGN % 3;
+    constexpr int NPASS = NP8 + (REM ? 1 : 0);
+    extern __shared__ __align__(16) unsigned char smz[];
+    C* sm = reinterpret_cast<C*>(smz);
+    const int gi = threadIdx.x / (PB * TPP);
+    const int rr = threadIdx.x % (PB * TPP);
+    const int pl = rr % PB, tp = rr / PB;
+    const int64_t col = (int64_t)blockIdx.x * PB + pl;
+    const bool valid = col < ncol;
+    C* A = sm + (int64_t)(gi * PB + pl) * 2 * pitch;
+    C* T = A + pitch;
+    // pass ps writes A when (NPASS - 1 - ps) is even, so the last lands in A
+    auto dst_of = [&](int ps) { return ((NPASS - 1 - ps) & 1) ? T : A; };
+    // kernel spectra of this thread's spectral-product points
+    constexpr int NT = 7 * PB * TPP;
+    constexpr int NPT = (PB * n + NT - 1) / NT;
+    C sp[NPT][4];
+#pragma unroll
+    for (int k = 0; k < NPT; k++) {
+        const int idx = threadIdx.x + k * NT;
+        const int p2 = idx % PB, kz = idx / PB;
+        const int64_t c2 = (int64_t)blockIdx.x * PB + p2;
+        if (idx < PB * n && c2 < ncol) {
+            const int64_t i = (int64_t)kz * plane + c2;
+#pragma unroll
+            for (int q = 0; q < 4; q++) sp[k][q] = spec[q * bnn + i];
+        }
+    }
+    // ---- forward: global (z < nz_phys, zero padded) -> ... -> A
+    int Ns = 1;
+    const int64_t gbase = gi * bnn + (valid ? col : 0);
+    stockham_pass<LOGN, 8, 0, 1, C, 0>(Ns, tp, buf, gbase, plane, nz_phys, nullptr, 0, 0, 0, valid, nullptr,
+                                       dst_of(0), tw);
+    Ns *= 8;
+    __syncthreads();
+    for (int ps = 1; ps < NP8; ps++) {
+        stockham_pass<LOGN, 8, 1, 1, C, 0>(Ns, tp, nullptr, 0, 0, 0, nullptr, 0, 0, 0, valid, dst_of(ps - 1),
+                                           dst_of(ps), tw);
+        Ns *= 8;
+        __syncthreads();
+    }
+    if constexpr (REM == 1)
+        stockham_pass<LOGN, 2, 1, 1, C, 0>(Ns, tp, nullptr, 0, 0, 0, nullptr, 0, 0, 0, valid, T, A, tw);
+    else if constexpr (REM == 2)
+        stockham_pass<LOGN, 4, 1, 1, C, 0>(Ns, tp, nullptr, 0, 0, 0, nullptr, 0, 0, 0, valid, T, A, tw);
+    if constexpr (REM != 0) __syncthreads();
+    // ---- spectral products, in place into A of grids 0..3 (kernel spectra
+    // loaded before the forward passes, so their latency overlaps them)
+#pragma unroll
+    for (int k = 0; k < NPT; k++) {
+        const int idx = threadIdx.x + k * NT;
+        if (idx >= PB * n) break;
+        const int p2 = idx % PB, kz = idx / PB;
+        const int64_t c2 = (int64_t)blockIdx.x * PB + p2;
+        if (c2 >= ncol) continue;
+        C in[7], out[4];
+#pragma unroll
+        for (int g = 0; g < 7; g++) in[g] = sm[(int64_t)(g * PB + p2) * 2 * pitch + kz];
+        sys_specmul(sp[k][0], sp[k][1], sp[k][2], sp[k][3], k0, in, out);
+#pragma unroll
+        for (int g = 0; g < 4; g++) sm[(int64_t)(g * PB + p2) * 2 * pitch + kz] = out[g];
+    }
+    __syncthreads();
+    // ---- inverse of grids 0..3: A -> T -> A ... -> global (z < nz_phys)
+    const bool act = gi < 4;
+    Ns = 1;
+    C* cur = A;
+    C* nxt = T;
+    if constexpr (NPASS == 1) {
+        if (act)
+            stockham_pass<LOGN, 8, 1, 0, C, 1>(Ns, tp, nullptr, 0, 0, 0, buf, gbase, plane, nz_phys, valid, A,
+                                               nullptr, tw);
+        return;
+    } else {
+        if (act)
+            stockham_pass<LOGN, 8, 1, 1, C, 1>(Ns, tp, nullptr, 0, 0, 0, nullptr, 0, 0, 0, valid, cur, nxt, tw);
+    }
+    Ns *= 8;
+    __syncthreads();
+    {
+        C* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    for (int ps = 1; ps < NP8; ps++) {
+        if (ps == NPASS - 1) {
+            if (act)
+                stockham_pass<LOGN, 8, 1, 0, C, 1>(Ns, tp, nullptr, 0, 0, 0, buf, gbase, plane, nz_phys, valid, cur,
+                                                   nullptr, tw);
+            return;
+        }
+        if (act)
+            stockham_pass<LOGN, 8, 1, 1, C, 1>(Ns, tp, nullptr, 0, 0, 0, nullptr, 0, 0, 0, valid, cur, nxt, tw);
+        Ns *= 8;
+        __syncthreads();
+        C* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if constexpr (REM == 1) {
+        if (act)
+            stockham_pass<LOGN, 2, 1, 0, C, 1>(Ns, tp, nullptr, 0, 0, 0, buf, gbase, plane, nz_phys, valid, cur,
+                                               nullptr, tw);
+    } else if constexpr (REM == 2) {
+        if (act)
+            stockham_pass<LOGN, 4, 1, 0, C, 1>(Ns, tp, nullptr, 0, 0, 0, buf, gbase, plane, nz_phys, valid, cur,
+                                               nullptr, tw);
+    }
+}
+
+template <int LOGN, int PB, class C, class R>
+static sie_status launch_z_sys_pb(cudaStream_t st, C* buf, const C* spec, const C* tw, int nz_phys, int64_t ncol,
+                                  int64_t plane, int64_t bnn, R k0)
+{
+    constexpr int n = 1 << LOGN;
+    const size_t smem = sizeof(C) * 7 * PB * 2 * (n + 1);
+    static const cudaError_t attr = cudaFuncSetAttribute(k_fft_z_sys<LOGN, PB, C, R>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    SIE_CUDA_TRY(attr);
+    const unsigned blocks = (unsigned)((ncol + PB - 1) / PB);
+    k_fft_z_sys<LOGN, PB, C, R><<<blocks, 7 * PB * n / 8, smem, st>>>(buf, spec, tw, nz_phys, ncol, plane, bnn, k0);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+// columns per CTA of k_fft_z_sys: 4 (complex64) or 2 (complex128) by default,
+// 57.8 KB of shared memory at n = 128; SIE_ZSYS_PB = 2, 4 or 8 overrides
+// (complex64; complex128 takes half of it, at least 1), for tuning
+static int zsys_pb(bool c64)
+{
+    static int forced = -1;
+    if (forced < 0) {
+        const char* e = getenv("SIE_ZSYS_PB");
+        forced = e ? atoi(e) : 0;
+    }
+    int pb = (forced == 2 || forced == 4 || forced == 8) ? forced : 4;
+    return c64 ? pb : std::max(1, pb / 2);
+}
+
+template <int LOGN, class C, class R>
+static sie_status launch_z_sys(cudaStream_t st, C* buf, const C* spec, int nz_phys, int64_t ncol, int64_t plane,
+                               int64_t bnn, R k0)
+{
+    C* tw = nullptr;
+    SIE_TRY(twiddles(LOGN, st, &tw));
+    const int pb = zsys_pb(sizeof(C) == 8);
+    if constexpr (sizeof(C) == 8) {
+        if (pb == 2) return launch_z_sys_pb<LOGN, 2, C, R>(st, buf, spec, tw, nz_phys, ncol, plane, bnn, k0);
+        if (pb == 8 && LOGN <= 7) return launch_z_sys_pb<LOGN, 8, C, R>(st, buf, spec, tw, nz_phys, ncol, plane, bnn, k0);
+        return launch_z_sys_pb<LOGN, 4, C, R>(st, buf, spec, tw, nz_phys, ncol, plane, bnn, k0);
+    } else {
+        if (pb == 1) return launch_z_sys_pb<LOGN, 1, C, R>(st, buf, spec, tw, nz_phys, ncol, plane, bnn, k0);
+        if (pb == 4 && LOGN <= 7) return launch_z_sys_pb<LOGN, 4, C, R>(st, buf, spec, tw, nz_phys, ncol, plane, bnn, k0);
+        return launch_z_sys_pb<LOGN, 2, C, R>(st, buf, spec, tw, nz_phys, ncol, plane, bnn, k0);
+    }
+}
+
 static int fft_kernel_choice()
 {
     static int k = -1;
@@ -722,6 +916,69 @@ sie_status fft3d(cudaStream_t st, float2* buf, const float2* src, const GridDesc
                  int nbatch)
 {
     return fft3d_t(st, buf, src, g, dir, prune, pc, nbatch);
+}
+
+// Grid part of the system product (Eq. sys) with the fused z stage: forward x
+// and y passes of the seven compact source grids in src (into buf), the fused
+// forward-z / spectral-product / inverse-z kernel, then the inverse y and x
+// passes of the four result grids back into the compact src.  Same arithmetic
+// as fft3d(-1) + k_specmul_sys + fft3d(+1), in another order of memory passes.
+template <class C, class R>
+static sie_status fft_sys_t(cudaStream_t st, C* buf, C* src, const GridDesc& g, const C* spec, R k0, sie_ctx* pc)
+{
+    const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int64_t Nx = g.N[0], Ny = g.N[1], Nz = g.N[2];
+    const int64_t pyz = nx * ny, bnn = nx * ny * nz, bNg = Nx * Ny * Nz;
+    PassGeom X{(int)Nx, (int)nx, Ny * Nz, (int)Ny, Nx, Nx * Ny, 1, nx, pyz, 1, 1, bNg, bnn};
+    {
+        Stage s_(pc, "fft_fwd_x");
+        SIE_TRY(launch_pass(st, (int)nx, src, buf, 0, X, 7));
+    }
+    PassGeom Y{(int)Ny, (int)ny, nx * Nz, (int)nx, 1, pyz, nx, 1, pyz, nx, 0, bnn, bnn};
+    {
+        Stage s_(pc, "fft_fwd_y");
+        SIE_TRY(launch_pass(st, (int)ny, buf, buf, 0, Y, 7));
+    }
+    {
+        Stage s_(pc, "fft_z_specmul");
+        sie_status s;
+        switch (nz) {
+            case 16: s = launch_z_sys<4>(st, buf, spec, (int)Nz, pyz, pyz, bnn, k0); break;
+            case 32: s = launch_z_sys<5>(st, buf, spec, (int)Nz, pyz, pyz, bnn, k0); break;
+            case 64: s = launch_z_sys<6>(st, buf, spec, (int)Nz, pyz, pyz, bnn, k0); break;
+            case 128: s = launch_z_sys<7>(st, buf, spec, (int)Nz, pyz, pyz, bnn, k0); break;
+            case 256: s = launch_z_sys<8>(st, buf, spec, (int)Nz, pyz, pyz, bnn, k0); break;
+            default:
+                set_error("fused z stage: unsupported FFT length");
+                return SIE_ERR_UNSUPPORTED;
+        }
+        SIE_TRY(s);
+    }
+    PassGeom Yi{(int)ny, (int)Ny, nx * Nz, (int)nx, 1, pyz, nx, 1, pyz, nx, 0, bnn, bnn};
+    {
+        Stage s_(pc, "fft_inv_y");
+        SIE_TRY(launch_pass(st, (int)ny, buf, buf, 1, Yi, 4));
+    }
+    PassGeom Xi{(int)nx, (int)Nx, Ny * Nz, (int)Ny, nx, pyz, 1, Nx, Nx * Ny, 1, 1, bnn, bNg};
+    {
+        Stage s_(pc, "fft_inv_x");
+        SIE_TRY(launch_pass(st, (int)nx, buf, src, 1, Xi, 4));
+    }
+    return SIE_OK;
+}
+
+bool fft_sys_supported(const GridDesc& g) { return g.n[2] >= 16 && g.n[2] <= 256; }
+
+sie_status fft_sys(cudaStream_t st, double2* buf, double2* src, const GridDesc& g, const double2* spec, double k0,
+                   sie_ctx* pc)
+{
+    return fft_sys_t(st, buf, src, g, spec, k0, pc);
+}
+
+sie_status fft_sys(cudaStream_t st, float2* buf, float2* src, const GridDesc& g, const float2* spec, float k0,
+                   sie_ctx* pc)
+{
+    return fft_sys_t(st, buf, src, g, spec, k0, pc);
 }
 
 // ------------------------------------------------------------------ kernel spectra
@@ -992,13 +1249,14 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
 static void free_aim(AimOp& a)
 {
     void* ptrs[] = {a.spec, a.spec32, a.pairs, a.row_ptr, a.col, a.valL, a.valK, a.valLA, a.dLA, a.dL,
-                    a.tri_row_ptr, a.tri_col, a.valLphi, a.valLphiNR, a.valM, a.valLA32, a.valK32, a.valLphi32,
+                    a.tri_row_ptr, a.tri_col, a.valLphi, a.valLphiNR, a.valM, a.valLK32, a.valLphi32,
                     a.obj_k, a.obj_ik2};
     a.obj_k = a.obj_ik2 = nullptr;
     for (void* p : ptrs)
         if (p) cudaFree(p);
     a.valLA = a.dLA = a.dL = a.valLphi = a.valLphiNR = a.valM = nullptr;
-    a.valLA32 = a.valK32 = a.valLphi32 = nullptr;
+    a.valLK32 = nullptr;
+    a.valLphi32 = nullptr;
     a.tri_row_ptr = nullptr;
     a.tri_col = nullptr;
     a.spec = nullptr;
@@ -1123,7 +1381,7 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
     {
         AimOp& X = op->ext;
         const int64_t ntri = X.tri_row_ptr_h.empty() ? 0 : X.tri_row_ptr_h.back();
-        if ((s = to_c64(st, X.valLA, X.nnz, &X.valLA32)) != SIE_OK || (s = to_c64(st, X.valK, X.nnz, &X.valK32)) != SIE_OK ||
+        if ((s = to_c64_pair(st, X.valLA, X.valK, X.nnz, &X.valLK32)) != SIE_OK ||
             (s = to_c64(st, X.valLphi, ntri, &X.valLphi32)) != SIE_OK)
             return fail(s);
     }

@@ -162,8 +162,7 @@ struct AimOp {
     double2* valLphiNR = nullptr;   // exact near Lphi (constraint preconditioner)
     double2* valM = nullptr;        // sparse approximate inverse of valL (near-only interiors)
     // complex64 copies of the exterior near values for the mixed-precision product
-    float2* valLA32 = nullptr;
-    float2* valK32 = nullptr;
+    float4* valLK32 = nullptr;      // (LA, K) of each stored entry, interleaved
     float2* valLphi32 = nullptr;
     // dense LU of the constraint triangle system (null: iterative constraint solve)
     DenseLU* lu = nullptr;
@@ -264,6 +263,8 @@ struct sie_op {
     double2* sys_E = nullptr;       // E' = Z' H (ne)
     double2* sys_tmp = nullptr;     // ne + 2 nt scratch
     double2* sys_vec = nullptr;     // 4 (ne + nt) scratch for host-pointer calls
+    float4* pk_he = nullptr;        // mixed near product: complex64 (H, E) side by side (ne)
+    float2* pk_sig = nullptr;       // mixed near product: complex64 triangle charges (nt)
     sie::KrylovWork kin, kout, kcs_in, kcs_out;
     double2 *cs_e = nullptr, *cs_t = nullptr, *pc_e = nullptr, *pc_t = nullptr;  // preconditioner scratch
     // last solve: outer iters, relres; max nested iters, relres; max constraint iters, relres
@@ -278,6 +279,8 @@ struct sie_op {
     double* gstat = nullptr;        // device: max nested iterations and residual of graph runs
     size_t gnodes[2] = {0, 0};      // nodes of the last captured graph: outside the loop, loop body
     double2* ir_buf = nullptr;      // iterative refinement: residual, correction, product (3 (ne + nt))
+    double q_w = 0.0;               // charge-row weight of the GMRES residual norm (0: not yet computed)
+    double2* bal = nullptr;         // weighted right-hand side and preconditioner input (2 (ne + nt))
     double lu_ms = 0;               // wall time of the dense constraint-preconditioner factorisations
     // surface impedance boundary condition (interior_model = SIE_SIBC): RWG Gram
     // matrix as edge CSR, its diagonal, and eta_i / eta0
@@ -342,6 +345,14 @@ sie_status constraint_lu_build(sie_op* op);
 void constraint_lu_release(sie_op* op);
 // SIE_ERR_TIMEOUT when a triangular-solve wait of a constraint LU ran out (synchronises)
 sie_status constraint_lu_check(sie_op* op);
+// grid part of the system product: forward x, y; fused forward z + spectral
+// products + inverse z; inverse y, x (seven source grids in the compact src,
+// four result grids back into it)
+bool fft_sys_supported(const GridDesc& g);  // z length 16 .. 256
+sie_status fft_sys(cudaStream_t st, double2* buf, double2* src, const GridDesc& g, const double2* spec, double k0,
+                   sie_ctx* pc);
+sie_status fft_sys(cudaStream_t st, float2* buf, float2* src, const GridDesc& g, const float2* spec, float k0,
+                   sie_ctx* pc);
 sie_status fft3d(cudaStream_t st, double2* buf, const double2* src, const GridDesc& g, int dir, int prune,
                  sie_ctx* prof_ctx, int nbatch = 1);
 sie_status fft3d(cudaStream_t st, float2* buf, const float2* src, const GridDesc& g, int dir, int prune,

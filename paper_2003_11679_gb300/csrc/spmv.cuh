@@ -13,9 +13,10 @@ namespace sie {
 
 // VT = double2: FP64 throughout.  VT = float2 (complex64 values of the mixed
 // precision path): FP32 products and per-lane sums, the group sum in FP64.
-template <int G, class VT>
+// XT: type of x (float2 with float2 values: no conversion in the inner loop)
+template <int G, class VT, class XT>
 __device__ __forceinline__ double2 csr_row_dot(int64_t e0, int64_t e1, const int32_t* __restrict__ col,
-                                               const VT* __restrict__ val, const double2* __restrict__ x, int l)
+                                               const VT* __restrict__ val, const XT* __restrict__ x, int l)
 {
     using R = decltype(VT{}.x);
     R ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};  // one set per unrolled slot (independent chains)
@@ -28,7 +29,7 @@ __device__ __forceinline__ double2 csr_row_dot(int64_t e0, int64_t e1, const int
             c[u] = __ldg(col + e + u * G);
             v[u] = __ldg(val + e + u * G);
         }
-        double2 xv[4];
+        XT xv[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) xv[u] = __ldg(x + c[u]);
 #pragma unroll
@@ -40,7 +41,7 @@ __device__ __forceinline__ double2 csr_row_dot(int64_t e0, int64_t e1, const int
     }
     for (; e < e1; e += G) {  // at most 3 more entries per lane
         VT v = __ldg(val + e);
-        double2 xd = __ldg(x + __ldg(col + e));
+        XT xd = __ldg(x + __ldg(col + e));
         const R xr = (R)xd.x, xi = (R)xd.y;
         ar[0] += v.x * xr - v.y * xi;
         ai[0] += v.x * xi + v.y * xr;
@@ -56,9 +57,9 @@ __device__ __forceinline__ double2 csr_row_dot(int64_t e0, int64_t e1, const int
 }
 
 // y = alpha A x (ACC = false) or y += alpha A x (ACC = true); blockDim 256
-template <int G, bool ACC, class VT>
+template <int G, bool ACC, class VT, class XT>
 __global__ void __launch_bounds__(256) k_csr(int nrow, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                             const VT* __restrict__ val, const double2* __restrict__ x,
+                                             const VT* __restrict__ val, const XT* __restrict__ x,
                                              double2 alpha, double2* __restrict__ y)
 {
     const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G);
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(256) k_csr(int nrow, const int64_t* __restrict
     const bool ok = r < nrow;
     // rows past the end still take part in the shuffles, with an empty range
     const int64_t e0 = ok ? __ldg(rp + r) : 0, e1 = ok ? __ldg(rp + r + 1) : 0;
-    const double2 s = csr_row_dot<G, VT>(e0, e1, col, val, x, l);
+    const double2 s = csr_row_dot<G, VT, XT>(e0, e1, col, val, x, l);
     if (ok && l == 0) {
         double2 t = make_double2(alpha.x * s.x - alpha.y * s.y, alpha.x * s.y + alpha.y * s.x);
         if (ACC) {
@@ -85,22 +86,22 @@ inline int csr_group(int64_t nrow, int64_t nnz)
     return avg <= 12 ? 4 : (avg <= 48 ? 8 : 32);
 }
 
-template <class VT>
+template <class VT, class XT>
 inline cudaError_t csr_launch(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp, const int32_t* col,
-                              const VT* val, const double2* x, double2 alpha, bool acc, double2* y)
+                              const VT* val, const XT* x, double2 alpha, bool acc, double2* y)
 {
     if (nrow <= 0) return cudaSuccess;
     const int G = csr_group(nrow, nnz);
     const unsigned blocks = (unsigned)(((int64_t)nrow * G + 255) / 256);
     if (G == 4) {
-        if (acc) k_csr<4, true, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
-        else k_csr<4, false, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+        if (acc) k_csr<4, true, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+        else k_csr<4, false, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
     } else if (G == 8) {
-        if (acc) k_csr<8, true, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
-        else k_csr<8, false, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+        if (acc) k_csr<8, true, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+        else k_csr<8, false, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
     } else {
-        if (acc) k_csr<32, true, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
-        else k_csr<32, false, VT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+        if (acc) k_csr<32, true, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+        else k_csr<32, false, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
     }
     return cudaGetLastError();
 }

@@ -14,11 +14,24 @@
 
 #include "internal.h"
 #include "spmv.cuh"
+#include "sysmul.cuh"
 
 namespace sie {
 
 using cplx = std::complex<double>;
 static const double C0 = 299792458.0, MU0 = 4e-7 * M_PI, ETA0 = MU0 * C0;
+
+// grid part of the system product with the fused z stage (default); SIE_FUSED_Z=0
+// in the environment keeps separate forward-z, spectral-multiply and inverse-z
+// launches (same arithmetic, for comparison)
+static bool fused_z()
+{
+    static const bool on = [] {
+        const char* e = getenv("SIE_FUSED_Z");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 // ------------------------------------------------------------------ vector kernels
 __global__ void k_axpby(int64_t n, double2 a, const double2* __restrict__ x, double2 b, double2* __restrict__ y)
@@ -761,17 +774,10 @@ __global__ void k_specmul_sys32(const float2* __restrict__ spec, float2* __restr
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
-    auto mul = [](float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
-    float2 G = spec[i], gx = spec[nn + i], gy = spec[2 * nn + i], gz = spec[3 * nn + i];
-    float2 jG = make_float2(-k0 * G.y, k0 * G.x);
-    float2 mx = buf[3 * nn + i], my = buf[4 * nn + i], mz = buf[5 * nn + i];
-    float2 cx = mul(gy, mz), cy = mul(gz, mx), cz = mul(gx, my);
-    float2 dx = mul(gz, my), dy = mul(gx, mz), dz = mul(gy, mx);
-    float2 a0 = mul(jG, buf[i]), a1 = mul(jG, buf[nn + i]), a2 = mul(jG, buf[2 * nn + i]);
-    buf[i] = make_float2(a0.x - (cx.x - dx.x), a0.y - (cx.y - dx.y));
-    buf[nn + i] = make_float2(a1.x - (cy.x - dy.x), a1.y - (cy.y - dy.y));
-    buf[2 * nn + i] = make_float2(a2.x - (cz.x - dz.x), a2.y - (cz.y - dz.y));
-    buf[3 * nn + i] = mul(G, buf[6 * nn + i]);
+    float2 in[7], out[4];
+    for (int g = 0; g < 7; g++) in[g] = buf[g * nn + i];
+    sys_specmul(spec[i], spec[nn + i], spec[2 * nn + i], spec[3 * nn + i], k0, in, out);
+    for (int g = 0; g < 4; g++) buf[g * nn + i] = out[g];
 }
 
 // W = P^T on the complex64 grids: FP32 gathers and sums, FP64 edge coefficients
@@ -837,26 +843,31 @@ __global__ void k_specmul_sys(const double2* __restrict__ spec, double2* __restr
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
-    auto mul = [](double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
-    double2 G = spec[i], gx = spec[nn + i], gy = spec[2 * nn + i], gz = spec[3 * nn + i];
-    double2 jG = make_double2(-k0 * G.y, k0 * G.x);  // j k0 G
-    double2 mx = buf[3 * nn + i], my = buf[4 * nn + i], mz = buf[5 * nn + i];
-    double2 cx = mul(gy, mz), cy = mul(gz, mx), cz = mul(gx, my);
-    double2 dx = mul(gz, my), dy = mul(gx, mz), dz = mul(gy, mx);
-    double2 a0 = mul(jG, buf[i]), a1 = mul(jG, buf[nn + i]), a2 = mul(jG, buf[2 * nn + i]);
-    buf[i] = make_double2(a0.x - (cx.x - dx.x), a0.y - (cx.y - dx.y));
-    buf[nn + i] = make_double2(a1.x - (cy.x - dy.x), a1.y - (cy.y - dy.y));
-    buf[2 * nn + i] = make_double2(a2.x - (cz.x - dz.x), a2.y - (cz.y - dz.y));
-    buf[3 * nn + i] = mul(G, buf[6 * nn + i]);
+    double2 in[7], out[4];
+    for (int g = 0; g < 7; g++) in[g] = buf[g * nn + i];
+    sys_specmul(spec[i], spec[nn + i], spec[2 * nn + i], spec[3 * nn + i], k0, in, out);
+    for (int g = 0; g < 4; g++) buf[g * nn + i] = out[g];
 }
 
-// k_spmv2 with complex64 values (SIE_MIXED): FP32 products and per-lane sums,
-// the lane sums combined in FP64
-__global__ void __launch_bounds__(128) k_spmv2_32(int nrow, const int64_t* __restrict__ rp,
-                                                  const int32_t* __restrict__ col, const float2* __restrict__ v1,
-                                                  const double2* __restrict__ x1, double2 a1,
-                                                  const float2* __restrict__ v2, const double2* __restrict__ x2,
-                                                  double2 a2, double2* __restrict__ y)
+// complex64 copies of H and E side by side for the mixed near product: one
+// 16-byte gather per stored entry instead of two 16-byte gathers and four
+// FP64 -> FP32 conversions (those run on the FP64 pipe)
+__global__ void k_pack_he32(int n, const double2* __restrict__ H, const double2* __restrict__ E,
+                            float4* __restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 h = H[i], e = E[i];
+    out[i] = make_float4((float)h.x, (float)h.y, (float)e.x, (float)e.y);
+}
+
+// k_spmv2 of the mixed path: the two matrices' complex64 values interleaved
+// (v[e] = (LA, K) of entry e: one 16-byte load), x packed by k_pack_he32;
+// FP32 products and per-lane sums, the lane sums combined in FP64
+__global__ void __launch_bounds__(128) k_spmv2_c64(int nrow, const int64_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ col, const float4* __restrict__ v,
+                                                   const float4* __restrict__ x, double2 a1, double2 a2,
+                                                   double2* __restrict__ y)
 {
     int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
@@ -866,33 +877,27 @@ __global__ void __launch_bounds__(128) k_spmv2_32(int nrow, const int64_t* __res
     int64_t e = e0 + lane;
     for (; e + 96 < e1; e += 128) {
         int c[4];
-        float2 p[4], q[4];
+        float4 p[4], q[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) c[u] = __ldg(col + e + 32 * u);
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            p[u] = __ldg(v1 + e + 32 * u);
-            q[u] = __ldg(v2 + e + 32 * u);
-        }
+        for (int u = 0; u < 4; u++) p[u] = __ldg(v + e + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; u++) q[u] = __ldg(x + c[u]);
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            double2 xa = __ldg(x1 + c[u]), xb = __ldg(x2 + c[u]);
-            float ar = (float)xa.x, ai = (float)xa.y, br = (float)xb.x, bi = (float)xb.y;
-            s1r += p[u].x * ar - p[u].y * ai;
-            s1i += p[u].x * ai + p[u].y * ar;
-            s2r += q[u].x * br - q[u].y * bi;
-            s2i += q[u].x * bi + q[u].y * br;
+            s1r += p[u].x * q[u].x - p[u].y * q[u].y;
+            s1i += p[u].x * q[u].y + p[u].y * q[u].x;
+            s2r += p[u].z * q[u].z - p[u].w * q[u].w;
+            s2i += p[u].z * q[u].w + p[u].w * q[u].z;
         }
     }
     for (; e < e1; e += 32) {
-        int c = col[e];
-        float2 p = v1[e], q = v2[e];
-        double2 xa = x1[c], xb = x2[c];
-        float ar = (float)xa.x, ai = (float)xa.y, br = (float)xb.x, bi = (float)xb.y;
-        s1r += p.x * ar - p.y * ai;
-        s1i += p.x * ai + p.y * ar;
-        s2r += q.x * br - q.y * bi;
-        s2i += q.x * bi + q.y * br;
+        float4 p = __ldg(v + e), q = __ldg(x + __ldg(col + e));
+        s1r += p.x * q.x - p.y * q.y;
+        s1i += p.x * q.y + p.y * q.x;
+        s2r += p.z * q.z - p.w * q.w;
+        s2i += p.z * q.w + p.w * q.z;
     }
     double t1r = s1r, t1i = s1i, t2r = s2r, t2i = s2i;
     for (int off = 16; off > 0; off >>= 1) {
@@ -988,6 +993,13 @@ __global__ void k_sigma(int nt, const double* __restrict__ area, const double2* 
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < nt) sig[t] = make_double2(-area[t] * rho[t].x, -area[t] * rho[t].y);
+}
+
+__global__ void k_sigma32(int nt, const double* __restrict__ area, const double2* __restrict__ rho,
+                          float2* __restrict__ sig)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nt) sig[t] = make_float2((float)(-area[t] * rho[t].x), (float)(-area[t] * rho[t].y));
 }
 
 __global__ void k_fdiv_area(int nt, const double* __restrict__ area, double2* __restrict__ x)
@@ -1344,13 +1356,17 @@ static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
                 op->pm_nnode, op->pm_node, op->pm_ptr, op->pm_ent, S, op->W32, tc, src, Ng);
             SIE_CUDA_TRY(cudaGetLastError());
         }
-        SIE_TRY(fft3d(st, buf, src, g, -1, 1, c, 7));
-        {
-            Stage s_(c, "specmul_sys32");
-            k_specmul_sys32<<<nb(nn), 256, 0, st>>>(X.spec32, buf, nn, (float)op->k0);
-            SIE_CUDA_TRY(cudaGetLastError());
+        if (fused_z() && fft_sys_supported(g)) {
+            SIE_TRY(fft_sys(st, buf, src, g, X.spec32, (float)op->k0, c));
+        } else {
+            SIE_TRY(fft3d(st, buf, src, g, -1, 1, c, 7));
+            {
+                Stage s_(c, "specmul_sys32");
+                k_specmul_sys32<<<nb(nn), 256, 0, st>>>(X.spec32, buf, nn, (float)op->k0);
+                SIE_CUDA_TRY(cudaGetLastError());
+            }
+            SIE_TRY(fft3d(st, buf, src, g, +1, 1, c, 4));
         }
-        SIE_TRY(fft3d(st, buf, src, g, +1, 1, c, 4));
         {
             Stage s_(c, "interp32");
             k_interp32<<<(M.nt + 3) / 4, 128, 0, st>>>(M.nt, S, g.M, M, op->base, op->W32, src, g, Ng, y1);
@@ -1368,13 +1384,17 @@ static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
                 op->pm_nnode, op->pm_node, op->pm_ptr, op->pm_ent, S, op->W, op->pm_tc, src, Ng);
             SIE_CUDA_TRY(cudaGetLastError());
         }
-        SIE_TRY(fft3d(st, buf, src, g, -1, 1, c, 7));
-        {
-            Stage s_(c, "specmul_sys");
-            k_specmul_sys<<<nb(nn), 256, 0, st>>>(X.spec, buf, nn, op->k0);
-            SIE_CUDA_TRY(cudaGetLastError());
+        if (fused_z() && fft_sys_supported(g)) {
+            SIE_TRY(fft_sys(st, buf, src, g, X.spec, op->k0, c));
+        } else {
+            SIE_TRY(fft3d(st, buf, src, g, -1, 1, c, 7));
+            {
+                Stage s_(c, "specmul_sys");
+                k_specmul_sys<<<nb(nn), 256, 0, st>>>(X.spec, buf, nn, op->k0);
+                SIE_CUDA_TRY(cudaGetLastError());
+            }
+            SIE_TRY(fft3d(st, buf, src, g, +1, 1, c, 4));
         }
-        SIE_TRY(fft3d(st, buf, src, g, +1, 1, c, 4));
         {
             Stage s_(c, "interp");
             SIE_TRY(aim_interp(op, src, 1, make_double2(1.0, 0.0), y1));
@@ -1382,26 +1402,30 @@ static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
     }
     {
         Stage s_(c, "spmv_sys");
-        const bool c64 = op->p.precision == SIE_MIXED && X.valLA32;
-        if (c64)
-            k_spmv2_32<<<(unsigned)((ne + 3) / 4), 128, 0, st>>>((int)ne, X.row_ptr, X.col, X.valLA32, H,
-                                                                  make_double2(0.0, op->k0), X.valK32, E,
-                                                                  make_double2(-1.0, 0.0), y1);
-        else
+        const bool c64 = op->p.precision == SIE_MIXED && X.valLK32;
+        if (c64) {
+            k_pack_he32<<<nb(ne), 256, 0, st>>>((int)ne, H, E, op->pk_he);
+            k_spmv2_c64<<<(unsigned)((ne + 3) / 4), 128, 0, st>>>((int)ne, X.row_ptr, X.col, X.valLK32, op->pk_he,
+                                                                   make_double2(0.0, op->k0),
+                                                                   make_double2(-1.0, 0.0), y1);
+        } else {
             k_spmv2<<<(unsigned)((ne + 3) / 4), 128, 0, st>>>((int)ne, X.row_ptr, X.col, X.valLA, H,
                                                                make_double2(0.0, op->k0), X.valK, E,
                                                                make_double2(-1.0, 0.0), y1);
+        }
         SIE_CUDA_TRY(cudaGetLastError());
         SIE_TRY(spmv(st, (int)ne, op->ix_nnz, op->ix_row_ptr, op->ix_col, op->ix_val, E, cplx(-0.5, 0.0), y1));
-        double2* sig = op->sys_tmp;
         double2* phi = op->sys_tmp + nt;
-        k_sigma<<<nb(nt), 256, 0, st>>>((int)nt, M.area, rho, sig);
-        if (c64)
-            SIE_CUDA_TRY(csr_launch(st, (int)nt, tri_nnz(X), X.tri_row_ptr, X.tri_col, X.valLphi32, sig,
+        if (c64) {
+            k_sigma32<<<nb(nt), 256, 0, st>>>((int)nt, M.area, rho, op->pk_sig);
+            SIE_CUDA_TRY(csr_launch(st, (int)nt, tri_nnz(X), X.tri_row_ptr, X.tri_col, X.valLphi32, op->pk_sig,
                                     make_double2(1.0, 0.0), false, phi));
-        else
+        } else {
+            double2* sig = op->sys_tmp;
+            k_sigma<<<nb(nt), 256, 0, st>>>((int)nt, M.area, rho, sig);
             SIE_TRY(spmv(st, (int)nt, tri_nnz(X), X.tri_row_ptr, X.tri_col, X.valLphi, sig, cplx(1.0, 0.0), phi,
                          false));
+        }
         k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, phi, y1);
         k_row2<<<nb(nt), 256, 0, st>>>((int)nt, M, H, rho, op->k0, y2);
         SIE_CUDA_TRY(cudaGetLastError());
@@ -1760,6 +1784,8 @@ sie_status sys_prepare(sie_op* op)
     SIE_CUDA_TRY(cudaMallocAsync((void**)&op->sys_E, sizeof(double2) * h.ne, st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&op->sys_tmp, sizeof(double2) * (h.ne + 2 * h.nt), st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&op->sys_vec, sizeof(double2) * 4 * (h.ne + h.nt), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->pk_he, sizeof(float4) * h.ne, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->pk_sig, sizeof(float2) * h.nt, st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&op->cs_e, sizeof(double2) * 2 * h.ne, st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&op->cs_t, sizeof(double2) * 3 * h.nt, st));
     SIE_CUDA_TRY(cudaMallocAsync((void**)&op->pc_e, sizeof(double2) * h.ne, st));
@@ -1790,8 +1816,12 @@ void sys_release(sie_op* op)
     op->kcs_in.release(st);
     op->kcs_out.release(st);
     for (void* p : {(void*)op->gr_row_ptr, (void*)op->gr_col, (void*)op->gr_val, (void*)op->gr_diag,
-                    (void*)op->pm_node, (void*)op->pm_ptr, (void*)op->pm_ent, (void*)op->pm_tc})
+                    (void*)op->pm_node, (void*)op->pm_ptr, (void*)op->pm_ent, (void*)op->pm_tc,
+                    (void*)op->pk_he, (void*)op->pk_sig, (void*)op->bal})
         if (p) cudaFreeAsync(p, st);
+    op->pk_he = nullptr;
+    op->pk_sig = nullptr;
+    op->bal = nullptr;
     for (void* p : {(void*)op->ix_row_ptr, (void*)op->ix_col, (void*)op->ix_val, (void*)op->elen, (void*)op->sys_E,
                     (void*)op->sys_tmp, (void*)op->sys_vec, (void*)op->cs_e, (void*)op->cs_t, (void*)op->pc_e,
                     (void*)op->pc_t})
@@ -1827,16 +1857,60 @@ sie_status nested_clear(sie_op* op)
     return SIE_OK;
 }
 
+// Row weighting of Eq. (sys) for the Krylov solves.  The charge rows
+// F D H + j k0 c0 rho are larger than the current rows by the ratio of a
+// divergence (~ 1 / edge length) to a Galerkin potential entry (~ area^2 G),
+// about 1e16 on the benchmark's copper sphere, so in the plain 2-norm of the
+// residual their FP64 rounding alone reaches 1e-3 of |b| and the Arnoldi
+// estimate loses touch with the true residual.  The Krylov solves therefore
+// use W A x = W b with W = diag(I, q_w I): q_w = mean_m |L_A,mm| makes the two
+// diagonal blocks of the constraint preconditioner, j k0 diag(L_A) and
+// j k0 I, the same size.  The solution is the same; tol_outer and the
+// reported relative residual refer to |W (b - A x)| / |W b|.
+static sie_status charge_weight(sie_op* op)
+{
+    if (op->q_w > 0) return SIE_OK;
+    cudaStream_t st = op->mesh->ctx->stream;
+    const int64_t ne = op->mesh->h.ne, n = ne + op->mesh->h.nt;
+    std::vector<double2> d(ne);
+    SIE_CUDA_TRY(cudaMemcpyAsync(d.data(), op->ext.dLA, sizeof(double2) * ne, cudaMemcpyDeviceToHost, st));
+    SIE_CUDA_TRY(cudaStreamSynchronize(st));
+    double sum = 0;
+    for (const double2& v : d) sum += std::hypot(v.x, v.y);
+    op->q_w = (ne > 0 && sum > 0 && std::isfinite(sum)) ? sum / (double)ne : 1.0;
+    if (!op->bal) SIE_CUDA_TRY(cudaMallocAsync((void**)&op->bal, sizeof(double2) * 2 * n, st));
+    return SIE_OK;
+}
+
+// v = W u (u, v may alias); with inv, v = W^-1 u
+static sie_status weight_rows(sie_op* op, const double2* u, double2* v, bool inv)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const int64_t ne = op->mesh->h.ne, nt = op->mesh->h.nt;
+    if (u != v) SIE_CUDA_TRY(cudaMemcpyAsync(v, u, sizeof(double2) * ne, cudaMemcpyDeviceToDevice, st));
+    return axpby(st, nt, inv ? 1.0 / op->q_w : op->q_w, u + ne, 0.0, v + ne);
+}
+
 sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres)
 {
     const int64_t n = op->mesh->h.ne + op->mesh->h.nt;
-    auto A = [&](const double2* u, double2* v) { return apply_sys_fast(op, u, v); };
-    auto Minv = [&](const double2* u, double2* v) { return precond_sys(op, u, v); };
+    SIE_TRY(charge_weight(op));
+    double2* bw = op->bal;
+    double2* tw = op->bal + n;
+    auto A = [&](const double2* u, double2* v) {
+        SIE_TRY(apply_sys_fast(op, u, v));
+        return weight_rows(op, v, v, false);
+    };
+    auto Minv = [&](const double2* u, double2* v) {
+        SIE_TRY(weight_rows(op, u, tw, true));
+        return precond_sys(op, tw, v);
+    };
     for (int i = 2; i < 6; i++) op->stats[i] = 0;
     if (op->gstat) SIE_CUDA_TRY(cudaMemsetAsync(op->gstat, 0, sizeof(double) * 2, op->mesh->ctx->stream));
+    SIE_TRY(weight_rows(op, b, bw, false));
     int it = 0;
     double rr = 0;
-    sie_status s = fgmres(op->mesh->ctx, op->kout, n, A, Minv, b, x, op->p.tol_outer, op->p.maxit, op->p.restart,
+    sie_status s = fgmres(op->mesh->ctx, op->kout, n, A, Minv, bw, x, op->p.tol_outer, op->p.maxit, op->p.restart,
                           &it, &rr);
     op->stats[0] = it;
     op->stats[1] = rr;
@@ -1880,13 +1954,23 @@ sie_status sys_solve_refined(sie_op* op, const double2* b, double2* x, int* iter
     double2* dot = op->kout.h;
     double* hbuf = op->kout.resid_h;
     const int saved = op->p.precision;
-    auto A32 = [&](const double2* u, double2* v) { return apply_sys_fast(op, u, v); };
-    auto Minv = [&](const double2* u, double2* v) { return precond_sys(op, u, v); };
+    SIE_TRY(charge_weight(op));
+    double2* tw = op->bal + n;
+    // both solves use the row-weighted system W A x = W b (charge_weight)
+    auto A32 = [&](const double2* u, double2* v) {
+        SIE_TRY(apply_sys_fast(op, u, v));
+        return weight_rows(op, v, v, false);
+    };
+    auto Minv = [&](const double2* u, double2* v) {
+        SIE_TRY(weight_rows(op, u, tw, true));
+        return precond_sys(op, tw, v);
+    };
     for (int i = 2; i < 6; i++) op->stats[i] = 0;
     if (op->gstat) SIE_CUDA_TRY(cudaMemsetAsync(op->gstat, 0, sizeof(double) * 2, st));
     SIE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
     double bn = 0, rel = 1.0;
-    SIE_TRY(norm2(st, n, b, part, dot, hbuf, &bn));
+    SIE_TRY(weight_rows(op, b, op->bal, false));
+    SIE_TRY(norm2(st, n, op->bal, part, dot, hbuf, &bn));
     int total = 0;
     sie_status s = SIE_OK;
     const int SWEEPS = 10;
@@ -1900,10 +1984,10 @@ sie_status sys_solve_refined(sie_op* op, const double2* b, double2* x, int* iter
         // FP64 residual
         op->p.precision = SIE_FP64;
         if (sweep == 0) {
-            SIE_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+            SIE_CUDA_TRY(cudaMemcpyAsync(r, op->bal, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
         } else {
-            if ((s = apply_sys_fast(op, x, t)) != SIE_OK) break;
-            SIE_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+            if ((s = A32(x, t)) != SIE_OK) break;
+            SIE_CUDA_TRY(cudaMemcpyAsync(r, op->bal, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
             if ((s = axpby(st, n, -1.0, t, 1.0, r)) != SIE_OK) break;
         }
         double rn = 0;

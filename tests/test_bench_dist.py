@@ -60,7 +60,7 @@ def _reference(rank, world):
     env = dict(os.environ, RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
                MASTER_ADDR="127.0.0.1", OMP_WAIT_POLICY="PASSIVE")
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
-           "dielectric-sphere-1920", "--steps", "1", "--warmup", "0", "--cpu-seconds", "0.5"]
+           "lossy-sphere-480", "--steps", "1", "--warmup", "0", "--cpu-seconds", "0.5"]
     return subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
 
 
