@@ -184,6 +184,10 @@ def stage_model(stage, info, ne, nt, nnz_ext, nnz_int):
         "spmv_near_only": (nnz_int * (c + 4) + (ne + 1) * 8 + 3 * ne * c, 8.0 * nnz_int),
         "spai_apply": (nnz_int * (c + 4) + (ne + 1) * 8 + 3 * ne * c, 8.0 * nnz_int),
         "specmul_sys": ((7 + 4 + 4) * nx * ny * nz * c, 8 * 10.0 * nx * ny * nz),
+        # fused forward z (7 grids) + spectral products + inverse z (4 grids):
+        # the z < Nz planes in and out, the 4 kernel spectra in
+        "fft_z_specmul": ((11 * nx * ny * Nz + 4 * nx * ny * nz) * c,
+                          11 * fl(nz, nx * ny) + 8 * 10.0 * nx * ny * nz),
         # two edge CSR products sharing the pattern (LA H and K E: 2 values + 1 col per nnz),
         # Ix E (5 nnz/row), triangle Lphi product (info[7] pairs), vectors
         "spmv_sys": (nnz_ext * (2 * c + 4) + 5 * ne * (c + 4) + int(info[7]) * (c + 4) + 8 * ne * c + 6 * nt * c,
@@ -318,6 +322,7 @@ def run_ours(args):
         block = block_stats(sie, op, ne, stream, args)
     solves = solve_stats(sie, ctx, args) if not args.no_solve else None
     lossy_solves = lossy_solve_stats(sie, op, args, wl) if not args.no_solve else None
+    serving = serving_stats(args) if (not args.no_solve and args.serve_requests > 0 and rank == 0) else None
     ms, e2e_s = combine_ranks(ms, e2e_s, world, f"cuda:{local}")
     if rank != 0:
         return
@@ -373,6 +378,7 @@ def run_ours(args):
                                  "loop); the stage breakdown comes from the stream path with per-stage events"},
         "solves": solves,
         "solves_workload": lossy_solves,
+        "serving": serving,
         "block_rhs": block,
         "mixed_precision": mixed_line(ne, args, ms32, prof32, mixed_err, info, peaks, kind),
         "stages_ms": {k: round(v[0], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
@@ -399,6 +405,7 @@ def mixed_line(ne, args, ms32, prof, err, info, peaks, kind):
              "fft_fwd_z": (nx * ny * Nz + nx * ny * nz) * c, "fft_inv_z": (nx * ny * nz + nx * ny * Nz) * c,
              "fft_inv_y": (nx * ny * Nz + nx * Ny * Nz) * c, "fft_inv_x": (nx * Ny * Nz + Nx * Ny * Nz) * c,
              "specmul_sys32": (7 + 4 + 4) * nx * ny * nz * c,
+             "fft_z_specmul": (11 * nx * ny * Nz + 4 * nx * ny * nz) * c,
              # complex64 exterior near values (LA, K; triangle Lphi), FP64 I-cross and vectors
              "spmv_sys": nnz_ext * (2 * c + 4) + ntri * (c + 4) + 5 * ne * 20 + 8 * ne * 16 + 6 * (n_t(info, ne)) * 16}
     kern = {k: v for k, v in prof.items() if k in model}
@@ -508,35 +515,119 @@ def block_stats(sie, op, ne, stream, args, R=8, reps=5):
 
 
 def lossy_solve_stats(sie, op, args, wl):
-    """GMRES solves of the timed workload itself (FP64, tol_outer 1e-4, Sec. V)
-    for seeded incidence directions: solves/s, latency, iterations, and each
-    solve's backscatter RCS against the Mie series (ok: converged and within
-    1%)."""
+    """GMRES solves of the timed workload itself (tol_outer 1e-4, Sec. V) for
+    seeded incidence directions: the FP64 solve and the mixed-precision
+    refinement (SIE_SOLVE_REFINE) on the same right-hand sides; solves/s,
+    latency, iterations, and each solve's backscatter RCS against the Mie
+    series (ok: converged and within 1%).  One untimed warm-up solve first
+    (graph capture, Krylov workspaces)."""
     ref = mie_backscatter(args.workload)
     rng = np.random.default_rng(11)
-    lat, its, errs, conv = [], [], [], []
+    dirs = []
     for i in range(args.lossy_solves):
         z = rng.uniform(-1, 1)
         ph = rng.uniform(0, 2 * np.pi)
         kh = np.array([np.sqrt(1 - z * z) * np.cos(ph), np.sqrt(1 - z * z) * np.sin(ph), z])
         ep = np.cross(kh, [0.3, -0.5, 0.8])
-        ep /= np.linalg.norm(ep)
-        b = op.rhs_planewave(kh, ep)
-        t0 = time.perf_counter()
-        x, it, rr = op.solve(b, check=False)
-        lat.append(time.perf_counter() - t0)
-        its.append(int(it[0]))
-        conv.append(bool(rr[0] < op_tol(sie)))
-        errs.append(float(op.rcs(x, -kh)[0] / ref - 1.0))
-    st = op.stats()
-    lat = np.array(lat)
-    return {"workload": args.workload, "tol": op_tol(sie), "solves": len(lat),
+        dirs.append((kh, ep / np.linalg.norm(ep)))
+    out = {"workload": args.workload, "tol": op_tol(sie), "solves": len(dirs), "mie_backscatter_m2": ref,
+           "dense_constraint_lu_ms": float(op.info()[19])}
+    for refine in (False, True):
+        if dirs:
+            op.solve(op.rhs_planewave(*dirs[0]), check=False, refine=refine)
+        lat, its, errs, conv = [], [], [], []
+        for kh, ep in dirs:
+            b = op.rhs_planewave(kh, ep)
+            t0 = time.perf_counter()
+            x, it, rr = op.solve(b, check=False, refine=refine)
+            lat.append(time.perf_counter() - t0)
+            its.append(int(it[0]))
+            conv.append(bool(rr[0] < op_tol(sie)))
+            errs.append(float(op.rcs(x, -kh)[0] / ref - 1.0))
+        lat = np.array(lat)
+        out["refined" if refine else "fp64"] = {
             "solves_per_s": float(len(lat) / lat.sum()) if len(lat) else None,
             "ok_solves": int(sum(c and abs(e) <= 0.01 for c, e in zip(conv, errs))),
             "not_converged": conv.count(False), "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_s": float(np.percentile(lat, 99)) if len(lat) else None, "iters": its,
-            "rcs_rel_err_vs_mie": errs, "mie_backscatter_m2": ref, "last_solve_stats": st,
-            "dense_constraint_lu_ms": float(op.info()[19])}
+            "rcs_rel_err_vs_mie": errs, "last_solve_stats": op.stats()}
+    if dirs:
+        out["refined_vs_fp64"] = {"speedup": out["refined"]["solves_per_s"] / out["fp64"]["solves_per_s"]}
+    return out
+
+
+def serve_catalogue():
+    """The serving trace's operators: (name, radius, f, eps_r, sigma, level,
+    Mie backscatter) as drawn and evaluated by tests/golden/make_mie_backscatter.py."""
+    path = os.path.join(ROOT, "tests", "golden", "mie_backscatter.txt")
+    out = []
+    for line in open(path):
+        f = line.split()
+        if f and f[0].startswith("serve-"):
+            out.append((f[0], float(f[1]), float(f[2]), float(f[3]), float(f[4]), int(f[0][-1]), float(f[5])))
+    return out
+
+
+def serving_stats(args):
+    """Serving trace (the serving configuration, scaled to one GPU for
+    minutes): args.serve_requests requests with Poisson arrivals at
+    args.serve_rate per second, each on one of the catalogue's operators
+    (uniform) with 1 to 4 plane waves (backscatter), through the request
+    loop (paper_2003_11679_gb300/serve.py: two slots, shared resident
+    operator cache, cross-request batching into lockstep solves).  Cold start:
+    the catalogue's operator builds fall in the trace.  Latency is per
+    request from its arrival; solves/s counts right-hand sides over the
+    trace's wall time; each solve's RCS is compared with the Mie series."""
+    from paper_2003_11679_gb300.serve import Request, Server
+    from synth import icosphere
+    cat = serve_catalogue()
+    rng = np.random.default_rng(17)
+    meshes = {c[0]: icosphere(c[5], c[1], equal_volume=True) for c in cat}
+    reqs, arrivals, t = [], [], 0.0
+    for i in range(args.serve_requests):
+        t += rng.exponential(1.0 / args.serve_rate)
+        c = cat[rng.integers(len(cat))]
+        k = int(rng.integers(1, 5))
+        khs, eps = [], []
+        for _ in range(k):
+            z = rng.uniform(-1, 1)
+            ph = rng.uniform(0, 2 * np.pi)
+            kh = np.array([np.sqrt(1 - z * z) * np.cos(ph), np.sqrt(1 - z * z) * np.sin(ph), z])
+            ep = np.cross(kh, [0.3, -0.5, 0.8])
+            khs.append(kh)
+            eps.append(ep / np.linalg.norm(ep))
+        V, T = meshes[c[0]]
+        r = Request(V, T, c[2], c[3], c[4], np.array(khs), np.array(eps), -np.array(khs))
+        reqs.append((r, c))
+        arrivals.append(t)
+    errs, res, nrhs = [], [], 0
+    with Server(slots=2) as srv:
+        t0 = time.perf_counter()
+        futs = []
+        for (r, c), ta in zip(reqs, arrivals):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            futs.append((srv.submit(r), r, c))
+        for f, r, c in futs:
+            out = f.result(timeout=1800)
+            rcs = np.atleast_2d(out["rcs"])
+            for q in range(r.nrhs):
+                errs.append(float(rcs[q, q] / c[6] - 1.0))  # backscatter: rhat_q = -khat_q
+            res.extend(np.atleast_1d(out["relres"]).tolist())
+            nrhs += r.nrhs
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    tol = 1e-4
+    ae = np.abs(errs)
+    return {"requests": len(reqs), "rate_per_s": args.serve_rate, "slots": 2, "operators": len(cat),
+            "right_hand_sides": nrhs, "wall_s": wall, "solves_per_s": nrhs / wall, "p50_s": st.get("p50_s"),
+            "p99_s": st.get("p99_s"), "built": st.get("built", 0), "reused": st.get("reused", 0),
+            "batched": st.get("batched", 0), "converged": int(sum(v < tol for v in res)),
+            "rcs_rel_err_vs_mie_p50": float(np.median(ae)), "rcs_rel_err_vs_mie_max": float(ae.max()),
+            "within_1pct": int((ae <= 0.01).sum()), "within_5pct": int((ae <= 0.05).sum()),
+            "note": "cold start: operator builds inside the trace; catalogue = tests/golden/mie_backscatter.txt "
+                    "serve-* rows (spheres, level 2-3 meshes)"}
 
 
 def op_tol(sie):
@@ -638,6 +729,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--solves", type=int, default=4)
     ap.add_argument("--lossy-solves", type=int, default=3)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--interior", default="gibc", choices=["gibc", "sibc"],
                     help="interior model of the timed operator (sibc: the surface impedance comparator)")
     args = ap.parse_args()

@@ -68,7 +68,8 @@ typedef struct sie_op sie_op;
 enum { SIE_FP64 = 0, SIE_MIXED = 1 };          /* grid-path precision */
 enum { SIE_GIBC = 0, SIE_SIBC = 1 };           /* interior model (sie_params.interior_model) */
 enum { SIE_DEVICE_PTRS = 1,                    /* flags: vector args are device pointers */
-       SIE_SOLVE_REFINE = 2 };                  /* sie_solve: mixed-precision iterative refinement */
+       SIE_SOLVE_REFINE = 2,                    /* sie_solve: mixed-precision iterative refinement */
+       SIE_SOLVE_SEQUENTIAL = 4 };              /* sie_solve: one right-hand side after another */
 
 /* Which operator sie_matvec applies. */
 enum {
@@ -95,8 +96,9 @@ typedef struct {
     int maxit;            /* outer iteration cap (800, Sec. V-A)                       */
     int restart;          /* GMRES restart length (100)                                */
     int inner_maxit;      /* nested iteration cap (200)                                */
-    double tol_constraint;/* constraint preconditioner: inner tolerance of its triangle
-                             (charge) system (1e-6)                                    */
+    double tol_constraint;/* constraint preconditioner: inner GMRES tolerance of its
+                             triangle (charge) system (1e-6), preconditioned by its
+                             dense factorisation when one was made (dense_pc_max) */
     int constraint_maxit; /* ... and its iteration cap (1000)                          */
     int constraint_restart; /* ... and its GMRES restart length (100)                  */
     double tol_constraint_inner; /* the same for the nested (interior) preconditioner (1e-3) */
@@ -287,6 +289,12 @@ sie_status sie_rhs_planewave(sie_op* op, const double* khat, const double* epol,
  * F D H + j k0 c0 rho alone reach 1e-3 of |b|.  b, x: complex128,
  * N_e + N_t per right-hand side ([H; c0 rho]), nrhs consecutive vectors.
  * iters / relres: per rhs (host arrays of nrhs, may be NULL).
+ * nrhs > 1: blocks of up to 8 right-hand sides are solved in lockstep (one
+ * Krylov basis each; every iteration applies the operator and the
+ * preconditioner to the block's current vectors together, the dense
+ * constraint factorisation in one pass over it for all of them) until all
+ * of the block have converged; iters then counts the block's iterations.
+ * SIE_SOLVE_SEQUENTIAL solves them one after another instead.
  * flags: SIE_DEVICE_PTRS; SIE_SOLVE_REFINE = mixed-precision iterative
  * refinement: the residual b - A x and the update use the FP64 product, each
  * correction A d = r is solved with the complex64 product (as SIE_MIXED) to
@@ -342,17 +350,19 @@ sie_status sie_rcs(sie_op* op, const double* x, const double* rhat, int ndir, do
  * direction, far-field sum and cross section that it reads back. */
 sie_status sie_rcs_static(sie_op* op, const double* x, const double* rhat, int ndir, double* rcs, int flags);
 
-/* x = A^-1 b for one dense complex matrix with the library's GPU LU, the one
- * the constraint preconditioners use (Sec. III-D: the paper factorises its
- * preconditioner by LU): complex64 blocked LU with partial pivoting on device
- * `device`, then either two triangular solves (flags 0) or, as the
- * preconditioners do, the explicit inverse U^-1 L^-1 P formed from the
- * factors and applied as one matrix-vector product (flags 1).  A: n x n
- * complex128 row-major (host), b, x: n complex128 (host); A is rounded to
- * complex64, so x carries complex64 rounding amplified by the condition
+/* x_q = A^-1 b_q for one dense complex matrix and nrhs right-hand sides with
+ * the library's GPU LU, the one the constraint preconditioners use
+ * (Sec. III-D: the paper factorises its preconditioner by LU): complex64
+ * blocked LU with partial pivoting on device `device`, then either two
+ * triangular solves per right-hand side (flags 0) or, as the preconditioners
+ * do, the explicit inverse U^-1 L^-1 P formed from the factors and applied in
+ * one pass over it per block of up to 8 right-hand sides (flags 1; one
+ * matrix-vector product each when n is odd).  A: n x n complex128 row-major
+ * (host), b, x: nrhs consecutive vectors of n complex128 (host); A is rounded
+ * to complex64, so x carries complex64 rounding amplified by the condition
  * number.  Allocates and frees its device memory; synchronises.  SIE_ERR_ARG
- * for n < 1 or a zero pivot (singular matrix). */
-sie_status sie_dense_solve(int device, int n, const double* A, const double* b, double* x, int flags);
+ * for n < 1, nrhs < 1 or a zero pivot (singular matrix). */
+sie_status sie_dense_solve(int device, int n, int nrhs, const double* A, const double* b, double* x, int flags);
 
 /* FMA throughput of device `device`: FP64 and FP32 TFLOP/s (2 flops per
  * FMA), measured by the library's own probe kernel (independent FMA chains on

@@ -23,6 +23,7 @@ SIE_FP64, SIE_MIXED = 0, 1
 SIE_GIBC, SIE_SIBC = 0, 1
 SIE_DEVICE_PTRS = 1
 SIE_SOLVE_REFINE = 2
+SIE_SOLVE_SEQUENTIAL = 4
 SIE_RCS_STATIC_MAX_DIR = 2048
 SIE_OP_L0, SIE_OP_K0, SIE_OP_LI, SIE_OP_KI, SIE_OP_SYS, SIE_OP_ZI = range(6)
 
@@ -91,7 +92,7 @@ def lib():
         L.sie_rcs.argtypes = [P, P, P, I, P, I]
         L.sie_rcs_static.argtypes = [P, P, P, I, P, I]
         L.sie_probe_fma.argtypes = [I, P, P]
-        L.sie_dense_solve.argtypes = [I, I, P, P, P, I]
+        L.sie_dense_solve.argtypes = [I, I, I, P, P, P, I]
         L.sie_mesh_create_objects.argtypes = [P, P, I64, P, I64, P, PP, P]
         L.sie_set_material.argtypes = [P, I, D, D, D]
         for name in SYMBOLS:
@@ -117,11 +118,14 @@ def probe_fma(device=0):
 def dense_solve(A, b, device=0, inverse=False):
     """x = A^-1 b with the library's GPU complex64 LU (verification of the
     factorisation the constraint preconditioners use); inverse=True applies
-    the explicit inverse formed from the factors, as the preconditioners do."""
+    the explicit inverse formed from the factors, as the preconditioners do.
+    b: one vector (n) or several ((nrhs, n), solved together)."""
     A = np.ascontiguousarray(A, dtype=np.complex128)
     b = np.ascontiguousarray(b, dtype=np.complex128)
     x = np.zeros_like(b)
-    _check(lib().sie_dense_solve(device, len(b), A.ctypes.data, b.ctypes.data, x.ctypes.data, 1 if inverse else 0))
+    n = A.shape[0]
+    nrhs = 1 if b.ndim == 1 else b.shape[0]
+    _check(lib().sie_dense_solve(device, n, nrhs, A.ctypes.data, b.ctypes.data, x.ctypes.data, 1 if inverse else 0))
     return x
 
 
@@ -277,16 +281,19 @@ class Operator:
                                        SIE_DEVICE_PTRS if dev else 0))
         return b
 
-    def solve(self, b, x=None, nrhs=1, check=True, refine=False):
+    def solve(self, b, x=None, nrhs=1, check=True, refine=False, sequential=False):
         """x = SYS^-1 b by FGMRES; returns (x, iters, relres).  refine=True: mixed-
-        precision iterative refinement (complex64 corrections, FP64 residuals)."""
+        precision iterative refinement (complex64 corrections, FP64 residuals).
+        nrhs > 1: b holds nrhs consecutive right-hand sides, solved in lockstep
+        blocks of up to 8 (sequential=True: one after another)."""
         if x is None:
             x = np.zeros_like(b)
         pb, db = _ptr(b)
         px, dx = _ptr(x)
         it = np.zeros(nrhs, np.int32)
         rr = np.zeros(nrhs)
-        flags = (SIE_DEVICE_PTRS if db else 0) | (SIE_SOLVE_REFINE if refine else 0)
+        flags = ((SIE_DEVICE_PTRS if db else 0) | (SIE_SOLVE_REFINE if refine else 0) |
+                 (SIE_SOLVE_SEQUENTIAL if sequential else 0))
         code = lib().sie_solve(self.h, pb, px, nrhs, it.ctypes.data, rr.ctypes.data, flags)
         if check or code != SIE_ERR_NOT_CONVERGED:
             _check(code)

@@ -1585,6 +1585,40 @@ sie_status sie_solve(sie_op* op, const double* b, double* x, int nrhs, int* iter
     cudaStream_t st = op->mesh->ctx->stream;
     const int64_t len = op->mesh->h.ne + op->mesh->h.nt;
     sie_status worst = SIE_OK;
+    if (nrhs > 1 && !(flags & SIE_SOLVE_SEQUENTIAL)) {
+        // blocks of up to 8 right-hand sides solved in lockstep
+        const bool dev = flags & SIE_DEVICE_PTRS;
+        if (!dev && !op->mvec)
+            SIE_CUDA_TRY(cudaMallocAsync((void**)&op->mvec, sizeof(double2) * 2 * 8 * len, st));
+        for (int r0 = 0; r0 < nrhs; r0 += 8) {
+            const int R = std::min(8, nrhs - r0);
+            const double2* bq[8];
+            double2* xq[8];
+            for (int q = 0; q < R; q++) {
+                if (dev) {
+                    bq[q] = (const double2*)b + (r0 + q) * len;
+                    xq[q] = (double2*)x + (r0 + q) * len;
+                } else {
+                    double2* bd = op->mvec + (int64_t)q * len;
+                    SIE_CUDA_TRY(cudaMemcpyAsync(bd, (const double2*)b + (r0 + q) * len, sizeof(double2) * len,
+                                                 cudaMemcpyHostToDevice, st));
+                    bq[q] = bd;
+                    xq[q] = op->mvec + (int64_t)(8 + q) * len;
+                }
+            }
+            sie_status s = sys_solve_multi(op, R, bq, xq, iters ? iters + r0 : nullptr,
+                                           relres ? relres + r0 : nullptr, (flags & SIE_SOLVE_REFINE) != 0);
+            if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
+            if (s == SIE_ERR_NOT_CONVERGED) worst = s;
+            if (!dev)
+                for (int q = 0; q < R; q++)
+                    SIE_CUDA_TRY(cudaMemcpyAsync((double2*)x + (r0 + q) * len, xq[q], sizeof(double2) * len,
+                                                 cudaMemcpyDeviceToHost, st));
+        }
+        SIE_CUDA_TRY(cudaStreamSynchronize(st));
+        if (worst != SIE_OK) set_error("sie_solve: GMRES reached maxit before the tolerance");
+        return worst;
+    }
     for (int r = 0; r < nrhs; r++) {
         const double2* br;
         double2* xr;

@@ -22,6 +22,8 @@
 #include <cmath>
 #include <vector>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace sie {
@@ -390,39 +392,155 @@ __global__ void k_perm_matrix(int n, const int* __restrict__ perm, float2* __res
 
 // y = X b for the explicit inverse X (row-major): a warp per row, FP32
 // products, the row sum in FP64; b complex128, converted on the fly
-__global__ void __launch_bounds__(256) k_cgemv_inv(int n, const float2* __restrict__ X, const double2* __restrict__ b,
+// x = X b for the explicit inverse X (complex64, n x n row-major); b first
+// converted to complex64 once (k_c128_to_c64), so the inner loop holds no
+// FP64 -> FP32 conversions (those run on the FP64 pipe).  One warp per GR
+// consecutive rows: each complex64 pair of b (one 16-byte load) serves GR
+// rows, so b is read n / GR times from L1/L2 instead of n times.  Lanes take
+// 16-byte (two-entry) slices of the rows; FP32 products and per-lane sums,
+// the warp sum in FP64.  Needs n even (16-byte aligned rows).
+constexpr int GEMV_GR = 4;
+__global__ void __launch_bounds__(256) k_cgemv_inv(int n, const float4* __restrict__ X, const float4* __restrict__ b,
                                                    double2* __restrict__ y)
+{
+    const int r0 = (blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * GEMV_GR;
+    const int lane = threadIdx.x & 31;
+    if (r0 >= n) return;
+    const int h = n / 2;  // float4 per row
+    float ar[GEMV_GR], ai[GEMV_GR];
+#pragma unroll
+    for (int g = 0; g < GEMV_GR; g++) ar[g] = ai[g] = 0.f;
+    const float4* rows[GEMV_GR];
+#pragma unroll
+    for (int g = 0; g < GEMV_GR; g++) rows[g] = X + (int64_t)min(r0 + g, n - 1) * h;
+    int c = lane;
+    for (; c + 32 < h; c += 64) {
+        float4 bv[2], a[2][GEMV_GR];
+#pragma unroll
+        for (int u = 0; u < 2; u++) bv[u] = __ldg(b + c + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+#pragma unroll
+            for (int g = 0; g < GEMV_GR; g++) a[u][g] = __ldg(rows[g] + c + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+#pragma unroll
+            for (int g = 0; g < GEMV_GR; g++) {
+                const float4 m = a[u][g], v = bv[u];
+                ar[g] = fmaf(m.x, v.x, fmaf(-m.y, v.y, fmaf(m.z, v.z, fmaf(-m.w, v.w, ar[g]))));
+                ai[g] = fmaf(m.x, v.y, fmaf(m.y, v.x, fmaf(m.z, v.w, fmaf(m.w, v.z, ai[g]))));
+            }
+    }
+    for (; c < h; c += 32) {
+        const float4 v = __ldg(b + c);
+#pragma unroll
+        for (int g = 0; g < GEMV_GR; g++) {
+            const float4 m = __ldg(rows[g] + c);
+            ar[g] = fmaf(m.x, v.x, fmaf(-m.y, v.y, fmaf(m.z, v.z, fmaf(-m.w, v.w, ar[g]))));
+            ai[g] = fmaf(m.x, v.y, fmaf(m.y, v.x, fmaf(m.z, v.w, fmaf(m.w, v.z, ai[g]))));
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < GEMV_GR; g++) {
+        double sr = ar[g], si = ai[g];
+        for (int off = 16; off > 0; off >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, off);
+            si += __shfl_xor_sync(0xffffffffu, si, off);
+        }
+        if (lane == 0 && r0 + g < n) y[r0 + g] = make_double2(sr, si);
+    }
+}
+
+// odd n: one warp per row, complex64 b
+__global__ void __launch_bounds__(256) k_cgemv_inv1(int n, const float2* __restrict__ X, const float2* __restrict__ b,
+                                                    double2* __restrict__ y)
 {
     const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
     const float2* row = X + (int64_t)r * n;
-    float ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
-    int c = lane;
-    for (; c + 96 < n; c += 128) {
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const float2 a = __ldg(row + c + 32 * u);
-            const double2 bv = __ldg(b + c + 32 * u);
-            const float br = (float)bv.x, bi = (float)bv.y;
-            ar[u] = fmaf(a.x, br, fmaf(-a.y, bi, ar[u]));
-            ai[u] = fmaf(a.x, bi, fmaf(a.y, br, ai[u]));
-        }
+    float ar = 0, ai = 0;
+    for (int c = lane; c < n; c += 32) {
+        const float2 a = __ldg(row + c), v = __ldg(b + c);
+        ar = fmaf(a.x, v.x, fmaf(-a.y, v.y, ar));
+        ai = fmaf(a.x, v.y, fmaf(a.y, v.x, ai));
     }
-    for (; c < n; c += 32) {
-        const float2 a = __ldg(row + c);
-        const double2 bv = __ldg(b + c);
-        const float br = (float)bv.x, bi = (float)bv.y;
-        ar[0] = fmaf(a.x, br, fmaf(-a.y, bi, ar[0]));
-        ai[0] = fmaf(a.x, bi, fmaf(a.y, br, ai[0]));
-    }
-    double sr = ((double)ar[0] + ar[1]) + ((double)ar[2] + ar[3]);
-    double si = ((double)ai[0] + ai[1]) + ((double)ai[2] + ai[3]);
+    double sr = ar, si = ai;
     for (int off = 16; off > 0; off >>= 1) {
         sr += __shfl_xor_sync(0xffffffffu, sr, off);
         si += __shfl_xor_sync(0xffffffffu, si, off);
     }
     if (lane == 0) y[r] = make_double2(sr, si);
+}
+
+// X B for up to MULTI_R right-hand sides at once (the explicit inverse read
+// once for all of them): B packed as R complex64 vectors of n (n even).  A CTA
+// takes MR_ROWS rows (4 per warp) and walks the columns in chunks of
+// MR_CHUNK entry pairs; each chunk of B (R x MR_CHUNK float4) is staged in
+// shared memory and read by every warp, the matrix streams from HBM once.
+// FP32 products and per-lane sums, warp sums in FP64; out: pointers to the R
+// complex128 results.
+constexpr int MULTI_R = 8;
+constexpr int MR_ROWS = 32;
+constexpr int MR_CHUNK = 128;
+struct OutPtrs {
+    double2* p[MULTI_R];
+};
+__global__ void __launch_bounds__(256, 2) k_cgemm_inv_multi(int n, int R, const float4* __restrict__ X,
+                                                         const float4* __restrict__ B, OutPtrs out)
+{
+    __shared__ float4 Bs[MULTI_R][MR_CHUNK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = blockIdx.x * MR_ROWS + warp * 4;
+    const int h = n / 2;
+    float ar[4][MULTI_R], ai[4][MULTI_R];
+#pragma unroll
+    for (int g = 0; g < 4; g++)
+#pragma unroll
+        for (int q = 0; q < MULTI_R; q++) ar[g][q] = ai[g][q] = 0.f;
+    const float4* rows[4];
+#pragma unroll
+    for (int g = 0; g < 4; g++) rows[g] = X + (int64_t)min(r0 + g, n - 1) * h;
+    for (int c0 = 0; c0 < h; c0 += MR_CHUNK) {
+        const int cl = min(MR_CHUNK, h - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < MULTI_R * MR_CHUNK; i += blockDim.x) {
+            const int q = i / MR_CHUNK, c = i % MR_CHUNK;
+            Bs[q][c] = (q < R && c < cl) ? B[(int64_t)q * h + c0 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        for (int c = lane; c < cl; c += 32) {
+            float4 m[4];
+#pragma unroll
+            for (int g = 0; g < 4; g++) m[g] = __ldg(rows[g] + c0 + c);
+#pragma unroll
+            for (int q = 0; q < MULTI_R; q++) {
+                const float4 v = Bs[q][c];
+#pragma unroll
+                for (int g = 0; g < 4; g++) {
+                    ar[g][q] = fmaf(m[g].x, v.x, fmaf(-m[g].y, v.y, fmaf(m[g].z, v.z, fmaf(-m[g].w, v.w, ar[g][q]))));
+                    ai[g][q] = fmaf(m[g].x, v.y, fmaf(m[g].y, v.x, fmaf(m[g].z, v.w, fmaf(m[g].w, v.z, ai[g][q]))));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < 4; g++)
+#pragma unroll
+        for (int q = 0; q < MULTI_R; q++) {
+            double sr = ar[g][q], si = ai[g][q];
+            for (int off = 16; off > 0; off >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, off);
+                si += __shfl_xor_sync(0xffffffffu, si, off);
+            }
+            if (lane == 0 && q < R && r0 + g < n) out.p[q][r0 + g] = make_double2(sr, si);
+        }
+}
+
+__global__ void k_c128_to_c64(int n, const double2* __restrict__ b, float2* __restrict__ y)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = make_float2((float)b[i].x, (float)b[i].y);
 }
 
 __global__ void k_perm_to_f32(int n, const int* __restrict__ perm, const double2* __restrict__ b,
@@ -445,9 +563,9 @@ __global__ void k_f32_to_f64(int n, const float2* __restrict__ a, double2* __res
 void DenseLU::release()
 {
     for (void* p : {(void*)A, (void*)Xinv, (void*)invL, (void*)invU, (void*)ipiv, (void*)perm, (void*)flags,
-                    (void*)counter, (void*)err, (void*)y0, (void*)y1, (void*)prow})
+                    (void*)counter, (void*)err, (void*)y0, (void*)y1, (void*)prow, (void*)bpack})
         if (p) cudaFree(p);
-    A = Xinv = invL = invU = y0 = y1 = prow = nullptr;
+    A = Xinv = invL = invU = y0 = y1 = prow = bpack = nullptr;
     ipiv = perm = flags = counter = err = nullptr;
     n = nblk = 0;
 }
@@ -549,7 +667,14 @@ sie_status DenseLU::invert(cudaStream_t st)
 sie_status DenseLU::solve(cudaStream_t st, const double2* b, double2* x)
 {
     if (Xinv) {
-        k_cgemv_inv<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, Xinv, b, x);
+        k_c128_to_c64<<<(n + 255) / 256, 256, 0, st>>>(n, b, y0);
+        if (n % 2 == 0) {
+            const int warps = (n + GEMV_GR - 1) / GEMV_GR;
+            k_cgemv_inv<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(n, reinterpret_cast<const float4*>(Xinv),
+                                                                    reinterpret_cast<const float4*>(y0), x);
+        } else {
+            k_cgemv_inv1<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, Xinv, y0, x);
+        }
         SIE_CUDA_TRY(cudaGetLastError());
         return SIE_OK;
     }
@@ -559,6 +684,30 @@ sie_status DenseLU::solve(cudaStream_t st, const double2* b, double2* x)
     k_trsv<<<nblk, 256, 0, st>>>(n, nblk, 0, A, n, invL, y0, y1, flags, epoch, counter, err);
     k_trsv<<<nblk, 256, 0, st>>>(n, nblk, 1, A, n, invU, y1, y0, flags + nblk, epoch, counter + 1, err);
     k_f32_to_f64<<<(n + 255) / 256, 256, 0, st>>>(n, y0, x);
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+// x_q = A^-1 b_q for R right-hand sides (R <= MULTI_R); with the explicit
+// inverse and n even one pass over it for all of them, else one solve each
+sie_status DenseLU::solve_multi(cudaStream_t st, int R, const double2* const* b, double2* const* x)
+{
+    if (R < 1 || R > MULTI_R) {
+        set_error("DenseLU::solve_multi: 1 to 8 right-hand sides");
+        return SIE_ERR_ARG;
+    }
+    if (!Xinv || n % 2 != 0 || R == 1) {
+        for (int q = 0; q < R; q++) SIE_TRY(solve(st, b[q], x[q]));
+        return SIE_OK;
+    }
+    if (!bpack) SIE_CUDA_TRY(cudaMalloc((void**)&bpack, sizeof(float2) * (size_t)MULTI_R * n));
+    OutPtrs o{};
+    for (int q = 0; q < R; q++) {
+        k_c128_to_c64<<<(n + 255) / 256, 256, 0, st>>>(n, b[q], bpack + (size_t)q * n);
+        o.p[q] = x[q];
+    }
+    k_cgemm_inv_multi<<<(unsigned)((n + MR_ROWS - 1) / MR_ROWS), 256, 0, st>>>(
+        n, R, reinterpret_cast<const float4*>(Xinv), reinterpret_cast<const float4*>(bpack), o);
     SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
 }
@@ -594,10 +743,11 @@ __global__ void k_f64_to_f32(int64_t n, const double2* __restrict__ a, float2* _
     if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
-extern "C" sie_status sie_dense_solve(int device, int n, const double* A, const double* b, double* x, int flags)
+extern "C" sie_status sie_dense_solve(int device, int n, int nrhs, const double* A, const double* b, double* x,
+                                      int flags)
 {
     using namespace sie;
-    if (n < 1 || !A || !b || !x) {
+    if (n < 1 || nrhs < 1 || !A || !b || !x) {
         set_error("sie_dense_solve: invalid argument");
         return SIE_ERR_ARG;
     }
@@ -614,24 +764,33 @@ extern "C" sie_status sie_dense_solve(int device, int n, const double* A, const 
         return r;
     };
     if ((s = f.alloc(n)) != SIE_OK) return done(s);
-    const size_t nn = (size_t)n * n;
+    const size_t nn = (size_t)n * n, nb = (size_t)n * nrhs;
     if (cudaMalloc((void**)&dA, sizeof(double2) * nn) != cudaSuccess ||
-        cudaMalloc((void**)&db, sizeof(double2) * n) != cudaSuccess ||
-        cudaMalloc((void**)&dx, sizeof(double2) * n) != cudaSuccess) {
+        cudaMalloc((void**)&db, sizeof(double2) * nb) != cudaSuccess ||
+        cudaMalloc((void**)&dx, sizeof(double2) * nb) != cudaSuccess) {
         set_error("sie_dense_solve: device allocation failed");
         return done(SIE_ERR_OOM);
     }
     if (cudaMemcpy(dA, A, sizeof(double2) * nn, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(db, b, sizeof(double2) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(db, b, sizeof(double2) * nb, cudaMemcpyHostToDevice) != cudaSuccess) {
         set_error("sie_dense_solve: copy failed");
         return done(SIE_ERR_CUDA);
     }
     k_f64_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>((int64_t)nn, dA, f.A);
     if ((s = f.factor(st)) != SIE_OK) return done(s);
     if ((flags & 1) && (s = f.invert(st)) != SIE_OK) return done(s);
-    if ((s = f.solve(st, db, dx)) != SIE_OK) return done(s);
+    for (int r0 = 0; r0 < nrhs; r0 += MULTI_R) {
+        const int R = std::min(MULTI_R, nrhs - r0);
+        const double2* bq[MULTI_R];
+        double2* xq[MULTI_R];
+        for (int q = 0; q < R; q++) {
+            bq[q] = db + (size_t)(r0 + q) * n;
+            xq[q] = dx + (size_t)(r0 + q) * n;
+        }
+        if ((s = f.solve_multi(st, R, bq, xq)) != SIE_OK) return done(s);
+    }
     if ((s = f.check(st)) != SIE_OK) return done(s);
-    if (cudaMemcpy(x, dx, sizeof(double2) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaMemcpy(x, dx, sizeof(double2) * nb, cudaMemcpyDeviceToHost) != cudaSuccess) {
         set_error("sie_dense_solve: copy failed");
         return done(SIE_ERR_CUDA);
     }

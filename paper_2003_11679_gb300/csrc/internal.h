@@ -126,11 +126,13 @@ struct DenseLU {
     int* counter = nullptr;   // 2: ticket counters of the two triangular solves
     int* err = nullptr;       // 1: a triangular-solve wait ran out; 2: zero pivot
     float2 *y0 = nullptr, *y1 = nullptr, *prow = nullptr;
+    float2* bpack = nullptr;  // up to 8 right-hand sides in complex64 (solve_multi)
     sie_status alloc(int n_);
     void release();
     sie_status factor(cudaStream_t st);
     sie_status invert(cudaStream_t st);
     sie_status solve(cudaStream_t st, const double2* b, double2* x);
+    sie_status solve_multi(cudaStream_t st, int R, const double2* const* b, double2* const* x);
     sie_status check(cudaStream_t st);
 };
 
@@ -266,6 +268,11 @@ struct sie_op {
     float4* pk_he = nullptr;        // mixed near product: complex64 (H, E) side by side (ne)
     float2* pk_sig = nullptr;       // mixed near product: complex64 triangle charges (nt)
     sie::KrylovWork kin, kout, kcs_in, kcs_out;
+    sie::KrylovWork kmulti[8];      // lockstep solves: one Krylov basis per right-hand side
+    sie::KrylovWork kcs_multi[8];   // ... and per triangle system of their constraint preconditioner
+    double2* mscr = nullptr;        // lockstep solves: per right-hand side scratch (8 blocks)
+    double2* ir_multi = nullptr;    // lockstep refinement: residuals, corrections, products (3 x 8 (ne + nt))
+    double2* mvec = nullptr;        // lockstep solves from host buffers: 2 x 8 (ne + nt)
     double2 *cs_e = nullptr, *cs_t = nullptr, *pc_e = nullptr, *pc_t = nullptr;  // preconditioner scratch
     // last solve: outer iters, relres; max nested iters, relres; max constraint iters, relres
     double stats[6] = {0, 0, 0, 0, 0, 0};
@@ -319,6 +326,8 @@ void sys_release(sie_op* op);
 sie_status sys_matvec(sie_op* op, int which, const double2* x, double2* y);
 sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres);
 sie_status sys_solve_refined(sie_op* op, const double2* b, double2* x, int* iters, double* relres);
+sie_status sys_solve_multi(sie_op* op, int R, const double2* const* b, double2* const* x, int* iters, double* relres,
+                           bool refine);
 sie_status sys_rhs(sie_op* op, const double* khat, const double* epol, double2* b);
 // y = A x for an edge CSR matrix (overwrites y)
 sie_status csr_mv(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp, const int32_t* col,

@@ -64,6 +64,7 @@ __global__ void k_jacobi(int64_t n, const double2* __restrict__ x, const double2
 // out[j] = sum_k conj(V[j][k]) w[k] for j < nv: pass 1 writes one partial per
 // (chunk, vector) block, pass 2 sums the partials of each vector in a fixed
 // order (deterministic, and spread over the whole GPU for long vectors)
+constexpr int MULTI_RHS = 8;    // right-hand sides per lockstep solve
 constexpr int DOT_CHUNKS = 64;
 constexpr int CGS_CHUNKS = 128;  // row chunks of the fused Gram-Schmidt kernels
 constexpr int CGS_TILE = 32;     // columns per shared-memory tile there
@@ -506,11 +507,13 @@ __global__ void k_gm_backsub(int jend, int m, const double2* __restrict__ H, con
 // monitored residual is the true residual of A x = b.  Arnoldi in FP64 with
 // classical Gram-Schmidt applied twice.  Everything stays on the device: the
 // Hessenberg column, the Givens rotations and the back substitution are tiny
-// kernels; the host reads each iteration's residual one iteration later
-// (event on a pinned copy), so the GPU does not wait on host round trips.
-// One extra iteration may run after convergence (it only lowers the residual).
+// kernels; the host reads each iteration's residual `lag` iterations later
+// (event on a pinned copy; lag 1 by default), so the GPU does not wait on
+// host round trips.  Then one extra iteration may run after convergence (it
+// only lowers the residual); short inner solves use lag 0 instead.
 static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, const Apply& Minv, const double2* b,
-                         double2* x, double tol, int maxit, int restart, int* iters_out, double* relres_out)
+                         double2* x, double tol, int maxit, int restart, int* iters_out, double* relres_out,
+                         int lag = 1)
 {
     cudaStream_t st = c->stream;
     SIE_TRY(K.alloc(st, n, restart));
@@ -531,7 +534,7 @@ static sie_status fgmres(sie_ctx* c, KrylovWork& K, int64_t n, const Apply& A, c
     SIE_CUDA_TRY(cudaGetLastError());
     int it = 0;
     double rel = 1.0;
-    const int LAG = 1;
+    const int LAG = lag;
     while (true) {
         int j = 0;
         bool conv = false;
@@ -1528,8 +1531,9 @@ void sys_stats_fold(sie_op* op)
 // with Dg = diag(LA) (exact diagonal) and Lphi_NR the exact near-region
 // scalar-potential matrix, by block elimination on the charges q = D y:
 //     (I - kappa D Dg^-1 D^T Lphi_NR) q = D Dg^-1 v,   y = Dg^-1 (v + kappa D^T Lphi_NR q),
-// the triangle system solved by an inner GMRES to a loose tolerance (the
-// outer iterations are flexible).
+// the triangle system solved by an inner GMRES to tol (the outer iterations
+// are flexible), preconditioned by its dense factorisation when one was made
+// (dense_pc_max).
 static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork& K, double tol, const double2* v,
                                    double2* y)
 {
@@ -1559,19 +1563,23 @@ static sie_status constraint_solve(sie_op* op, AimOp& a, cplx kappa, KrylovWork&
         SIE_CUDA_TRY(cudaMemcpyAsync(out, x, sizeof(double2) * nt, cudaMemcpyDeviceToDevice, st));
         return SIE_OK;
     };
-    // with a dense LU of the triangle system (complex64) it preconditions the
-    // GMRES, which then needs a few iterations; without it, the identity
     auto LU = [&](const double2* x, double2* out) {
         Stage s_(c, "constraint_lu_solve");
         return a.lu->solve(st, x, out);
     };
+    // the dense LU (complex64 assembly and factors) preconditions a GMRES on
+    // the FP64 triangle system, which then converges in two or three
+    // iterations; applied alone it is not enough: T = I - kappa D Dg^-1 D^T
+    // Lphi has entries far above 1 whose cancellation the complex64 copy
+    // loses, and the outer solve stalls.  Without the LU, plain GMRES.
     const Apply P = a.lu ? Apply(LU) : Apply(I);
     int it = 0;
     double rr = 0;
     sie_status s;
     {
         Stage s_(c, "constraint_solve");
-        s = fgmres(c, K, nt, S, P, rq, q, tol, op->p.constraint_maxit, op->p.constraint_restart, &it, &rr);
+        // a handful of iterations: each checked before the next (lag 0)
+        s = fgmres(c, K, nt, S, P, rq, q, tol, op->p.constraint_maxit, op->p.constraint_restart, &it, &rr, 0);
     }
     op->stats[4] = std::max(op->stats[4], (double)it);
     op->stats[5] = std::max(op->stats[5], rr);
@@ -1813,6 +1821,11 @@ void sys_release(sie_op* op)
     op->gstat = nullptr;
     op->kin.release(st);
     op->kout.release(st);
+    for (KrylovWork& k : op->kmulti) k.release(st);
+    for (KrylovWork& k : op->kcs_multi) k.release(st);
+    for (void* p : {(void*)op->mscr, (void*)op->ir_multi, (void*)op->mvec})
+        if (p) cudaFreeAsync(p, st);
+    op->mscr = op->ir_multi = op->mvec = nullptr;
     op->kcs_in.release(st);
     op->kcs_out.release(st);
     for (void* p : {(void*)op->gr_row_ptr, (void*)op->gr_col, (void*)op->gr_val, (void*)op->gr_diag,
@@ -2093,6 +2106,361 @@ sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int 
     k_far<<<ndir, 256, 0, st>>>(op->mesh->d.nt, op->mesh->d, gl_rule(6), op->k0, rhat_d, x, op->sys_E, sums);
     SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
+}
+
+// ------------------------------------------------------------------ several right-hand sides in lockstep
+// y_q = Op x_q for q < R: a non-owning reference to a block operator
+class BlockApply {
+    const void* obj_ = nullptr;
+    sie_status (*call_)(const void*, int, const double2* const*, double2* const*) = nullptr;
+
+public:
+    template <class F>
+    BlockApply(const F& f)  // NOLINT: implicit from a named callable
+        : obj_(&f), call_([](const void* o, int R, const double2* const* x, double2* const* y) {
+              return (*static_cast<const F*>(o))(R, x, y);
+          })
+    {
+    }
+    sie_status operator()(int R, const double2* const* x, double2* const* y) const { return call_(obj_, R, x, y); }
+};
+
+// R restarted flexible GMRES iterations in lockstep: one Krylov basis per
+// right-hand side (K[q]), the operator and the preconditioner applied to the
+// R current vectors at once (so a block implementation reads its data once
+// for all of them), the Gram-Schmidt, Givens and update steps of fgmres per
+// right-hand side.  The cycle ends when every residual is below tol (a
+// converged right-hand side keeps iterating with the others, which only lowers
+// its residual); restarts from the true residuals.  iters: iterations run
+// (the same for all), relres[q]: final relative residual of q.
+static sie_status fgmres_multi(sie_ctx* c, KrylovWork* K, int R, int64_t n, const BlockApply& A,
+                               const BlockApply& Minv, const double2* const* b, double2* const* x, double tol,
+                               int maxit, int restart, int* iters_out, double* relres_out, int lag = 1)
+{
+    cudaStream_t st = c->stream;
+    const int m = restart;
+    for (int q = 0; q < R; q++) SIE_TRY(K[q].alloc(st, n, restart));
+    auto H = [&](int q) { return K[q].Hd; };
+    auto cs = [&](int q) { return K[q].Hd + (m + 1) * m; };
+    auto sn = [&](int q) { return K[q].Hd + (m + 1) * m + m; };
+    auto g = [&](int q) { return K[q].Hd + (m + 1) * m + 2 * m; };
+    auto y = [&](int q) { return K[q].Hd + (m + 1) * m + 2 * m + (m + 1); };
+    auto wd = [&](int q) { return K[q].h + 2 * (m + 2); };
+    for (int q = 0; q < R; q++) {
+        SIE_CUDA_TRY(cudaMemsetAsync(x[q], 0, sizeof(double2) * n, st));
+        SIE_TRY(dots(st, n, 1, b[q], n, b[q], K[q].part, wd(q)));
+        k_gm_start<<<nb(n), 256, 0, st>>>(n, b[q], wd(q), K[q].V, g(q), m, K[q].sc, 1);
+    }
+    SIE_CUDA_TRY(cudaGetLastError());
+    int it = 0;
+    double rel[MULTI_RHS];
+    for (int q = 0; q < R; q++) rel[q] = 1.0;
+    const int LAG = lag;
+    auto all_below = [&](const double* v) {
+        for (int q = 0; q < R; q++)
+            if (!(v[q] < tol)) return false;
+        return true;
+    };
+    while (true) {
+        int j = 0;
+        bool conv = false;
+        for (; j < m && it < maxit; j++) {
+            const double2* vj[MULTI_RHS];
+            double2 *zj[MULTI_RHS], *wq[MULTI_RHS];
+            for (int q = 0; q < R; q++) {
+                vj[q] = K[q].V + (int64_t)j * n;
+                zj[q] = K[q].Z + (int64_t)j * n;
+                wq[q] = K[q].w;
+            }
+            SIE_TRY(Minv(R, vj, zj));
+            SIE_TRY(A(R, zj, wq));
+            for (int q = 0; q < R; q++) {
+                double2* P1 = K[q].cgsp;
+                double2* P2 = K[q].cgsp + (int64_t)CGS_CHUNKS * (m + 1);
+                double2* P3 = K[q].cgsp + (int64_t)2 * CGS_CHUNKS * (m + 1);
+                double2* h1 = K[q].h;
+                double2* h2 = K[q].h + (m + 2);
+                k_cgs_part<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K[q].V, n, K[q].w, P1, m + 1, nullptr, nullptr,
+                                                       nullptr);
+                k_cgs_update<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K[q].V, n, P1, m + 1, h1, K[q].w, P2, 0, nullptr);
+                k_cgs_update<<<CGS_CHUNKS, 256, 0, st>>>(n, j + 1, K[q].V, n, P2, m + 1, h2, K[q].w, P3, 1, nullptr);
+                k_cgs_finish<<<CGS_CHUNKS, 256, 0, st>>>(n, j, m, h1, h2, P3, K[q].w, K[q].V, H(q), cs(q), sn(q),
+                                                         g(q), K[q].sc, nullptr);
+                SIE_CUDA_TRY(cudaMemcpyAsync(K[q].resid_h + j, K[q].sc + 3 + j, sizeof(double),
+                                             cudaMemcpyDeviceToHost, st));
+            }
+            SIE_CUDA_TRY(cudaGetLastError());
+            SIE_CUDA_TRY(cudaEventRecord(K[0].ev[j], st));
+            it++;
+            if (j >= LAG) {
+                SIE_CUDA_TRY(cudaEventSynchronize(K[0].ev[j - LAG]));
+                double v[MULTI_RHS];
+                for (int q = 0; q < R; q++) {
+                    v[q] = K[q].resid_h[j - LAG];
+                    if (!std::isfinite(v[q])) {
+                        set_error("GMRES: the residual is not finite (non-finite right-hand side or operator)");
+                        return SIE_ERR_ARG;
+                    }
+                }
+                if (all_below(v)) {
+                    conv = true;
+                    j++;
+                    break;
+                }
+            }
+        }
+        const int jend = j - 1;
+        SIE_CUDA_TRY(cudaEventSynchronize(K[0].ev[jend]));
+        for (int q = 0; q < R; q++) {
+            rel[q] = K[q].resid_h[jend];
+            if (!std::isfinite(rel[q])) {
+                set_error("GMRES: the residual is not finite (non-finite right-hand side or operator)");
+                return SIE_ERR_ARG;
+            }
+            k_gm_backsub<<<1, 1, 0, st>>>(jend, m, H(q), g(q), y(q));
+            k_gemv<<<nb(n), 256, 0, st>>>(n, jend + 1, K[q].Z, n, y(q), 1.0, x[q]);
+        }
+        SIE_CUDA_TRY(cudaGetLastError());
+        if (all_below(rel)) conv = true;
+        if (conv || it >= maxit) break;
+        // restart from the true residuals
+        double2* wq[MULTI_RHS];
+        for (int q = 0; q < R; q++) wq[q] = K[q].w;
+        SIE_TRY(A(R, x, wq));
+        for (int q = 0; q < R; q++) {
+            SIE_CUDA_TRY(cudaMemcpyAsync(K[q].r, b[q], sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+            SIE_TRY(axpby(st, n, -1.0, K[q].w, 1.0, K[q].r));
+            SIE_TRY(dots(st, n, 1, K[q].r, n, K[q].r, K[q].part, wd(q)));
+            k_gm_start<<<nb(n), 256, 0, st>>>(n, K[q].r, wd(q), K[q].V, g(q), m, K[q].sc, 0);
+            SIE_CUDA_TRY(cudaMemcpyAsync(K[q].resid_h, K[q].sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        SIE_CUDA_TRY(cudaGetLastError());
+        SIE_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int q = 0; q < R; q++) rel[q] = K[q].resid_h[0] > 0 ? K[q].resid_h[1] / K[q].resid_h[0] : 0.0;
+        if (all_below(rel)) break;
+    }
+    for (int q = 0; q < R; q++) {
+        if (iters_out) iters_out[q] = it;
+        if (relres_out) relres_out[q] = rel[q];
+    }
+    return all_below(rel) ? SIE_OK : SIE_ERR_NOT_CONVERGED;
+}
+
+// scratch of the lockstep solves: per right-hand side the weighted input of
+// the preconditioner, the weighted right-hand side and the preconditioner's
+// vectors (ne: v1', t1, te and the triangle operator's te; nt: sigma, phi,
+// charge rhs, charges and the triangle operator's phi)
+static int64_t multi_stride(const sie_op* op)
+{
+    return 2 * (op->mesh->h.ne + op->mesh->h.nt) + 4 * op->mesh->h.ne + 5 * op->mesh->h.nt;
+}
+
+static sie_status multi_scratch(sie_op* op)
+{
+    if (op->mscr) return SIE_OK;
+    const int64_t n = op->mesh->h.ne + op->mesh->h.nt;
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->mscr, sizeof(double2) * MULTI_RHS * multi_stride(op),
+                                 op->mesh->ctx->stream));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&op->ir_multi, sizeof(double2) * 3 * MULTI_RHS * n, op->mesh->ctx->stream));
+    return SIE_OK;
+}
+
+// the constraint preconditioner (precond_sys) for R vectors: the sparse
+// steps per vector, the R triangle systems by lockstep GMRES whose
+// preconditioner is one pass over the dense inverse for all of them
+// (DenseLU::solve_multi); without a factorisation, precond_sys for each
+static sie_status precond_sys_multi(sie_op* op, int R, const double2* const* x, double2* const* y)
+{
+    AimOp& X = op->ext;
+    if (!X.lu) {
+        for (int q = 0; q < R; q++) SIE_TRY(precond_sys(op, x[q], y[q]));
+        return SIE_OK;
+    }
+    sie_ctx* c = op->mesh->ctx;
+    cudaStream_t st = c->stream;
+    const DevMesh& M = op->mesh->d;
+    const int64_t ne = M.ne, nt = M.nt, n = ne + nt;
+    const cplx jk0(0.0, op->k0);
+    const cplx kappa = 1.0 / (op->k0 * op->k0);
+    double2 *v1p[MULTI_RHS], *t1[MULTI_RHS], *te[MULTI_RHS], *sig[MULTI_RHS], *ph[MULTI_RHS];
+    double2 *rq[MULTI_RHS], *qv[MULTI_RHS], *ste[MULTI_RHS], *sph[MULTI_RHS];
+    for (int q = 0; q < R; q++) {
+        double2* base = op->mscr + q * multi_stride(op) + 2 * n;
+        v1p[q] = base;
+        t1[q] = base + ne;
+        te[q] = base + 2 * ne;
+        ste[q] = base + 3 * ne;
+        sig[q] = base + 4 * ne;
+        ph[q] = sig[q] + nt;
+        rq[q] = ph[q] + nt;
+        qv[q] = rq[q] + nt;
+        sph[q] = qv[q] + nt;
+    }
+    for (int q = 0; q < R; q++) {
+        // v1' = v1 - (j k0)^-1 D^T Lphi B v2, then the charge right-hand side D Dg^-1 v1'
+        k_sigma<<<nb(nt), 256, 0, st>>>((int)nt, M.area, x[q] + ne, sig[q]);
+        SIE_TRY(spmv(st, (int)nt, tri_nnz(X), X.tri_row_ptr, X.tri_col, X.valLphiNR, sig[q], 1.0, ph[q], false));
+        SIE_CUDA_TRY(cudaMemsetAsync(v1p[q], 0, sizeof(double2) * ne, st));
+        k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, ph[q], v1p[q]);
+        SIE_TRY(axpby(st, ne, 1.0, x[q], -1.0 / jk0, v1p[q]));
+        k_jacobi<<<nb(ne), 256, 0, st>>>(ne, v1p[q], X.dLA, make_double2(1.0, 0.0), t1[q]);
+        k_D<<<nb(nt), 256, 0, st>>>((int)nt, M, t1[q], rq[q]);
+    }
+    SIE_CUDA_TRY(cudaGetLastError());
+    // triangle operator S q = q - kappa D Dg^-1 D^T Lphi q for each vector
+    auto S = [&](int Rn, const double2* const* u, double2* const* v) {
+        for (int q = 0; q < Rn; q++) {
+            SIE_TRY(spmv(st, (int)nt, tri_nnz(X), X.tri_row_ptr, X.tri_col, X.valLphiNR, u[q], 1.0, sph[q], false));
+            SIE_CUDA_TRY(cudaMemsetAsync(ste[q], 0, sizeof(double2) * ne, st));
+            k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, sph[q], ste[q]);
+            k_jacobi<<<nb(ne), 256, 0, st>>>(ne, ste[q], X.dLA, make_double2(1.0, 0.0), ste[q]);
+            k_D<<<nb(nt), 256, 0, st>>>((int)nt, M, ste[q], v[q]);
+            SIE_CUDA_TRY(cudaGetLastError());
+            SIE_TRY(axpby(st, nt, 1.0, u[q], -kappa, v[q]));
+        }
+        return SIE_OK;
+    };
+    auto LU = [&](int Rn, const double2* const* u, double2* const* v) {
+        Stage s_(c, "constraint_lu_solve");
+        return X.lu->solve_multi(st, Rn, u, v);
+    };
+    {
+        int it[MULTI_RHS];
+        double rr[MULTI_RHS];
+        Stage s_(c, "constraint_solve");
+        sie_status s = fgmres_multi(c, op->kcs_multi, R, nt, S, LU, rq, qv, op->p.tol_constraint,
+                                    op->p.constraint_maxit, std::min(op->p.constraint_restart, 20), it, rr, 0);
+        if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
+        for (int q = 0; q < R; q++) {
+            op->stats[4] = std::max(op->stats[4], (double)it[q]);
+            op->stats[5] = std::max(op->stats[5], rr[q]);
+        }
+    }
+    for (int q = 0; q < R; q++) {
+        // y1 = (j k0)^-1 Dg^-1 (v1' + kappa D^T Lphi q)
+        SIE_TRY(spmv(st, (int)nt, tri_nnz(X), X.tri_row_ptr, X.tri_col, X.valLphiNR, qv[q], 1.0, ph[q], false));
+        SIE_CUDA_TRY(cudaMemsetAsync(te[q], 0, sizeof(double2) * ne, st));
+        k_dt<<<nb(ne), 256, 0, st>>>((int)ne, M.edge_tri, op->elen, ph[q], te[q]);
+        SIE_TRY(axpby(st, ne, kappa, te[q], 0.0, te[q]));
+        SIE_TRY(axpby(st, ne, 1.0, v1p[q], 1.0, te[q]));
+        k_jacobi<<<nb(ne), 256, 0, st>>>(ne, te[q], X.dLA, make_double2(1.0, 0.0), y[q]);
+        SIE_TRY(axpby(st, ne, 1.0 / jk0, y[q], 0.0, y[q]));
+        // y2 = (v2 - F D y1) / (j k0)
+        k_D<<<nb(nt), 256, 0, st>>>((int)nt, M, y[q], ph[q]);
+        k_fdiv_area<<<nb(nt), 256, 0, st>>>((int)nt, M.area, ph[q]);
+        SIE_CUDA_TRY(cudaMemcpyAsync(y[q] + ne, x[q] + ne, sizeof(double2) * nt, cudaMemcpyDeviceToDevice, st));
+        SIE_TRY(axpby(st, nt, -1.0 / jk0, ph[q], 1.0 / jk0, y[q] + ne));
+    }
+    SIE_CUDA_TRY(cudaGetLastError());
+    return SIE_OK;
+}
+
+// Eq. (sys) for R right-hand sides in lockstep (row-weighted as in sys_solve):
+// plain FP64 FGMRES, or (refine) the mixed-precision refinement of
+// sys_solve_refined with every sweep's corrections solved in lockstep.
+// iters[q], relres[q] as for one right-hand side.
+sie_status sys_solve_multi(sie_op* op, int R, const double2* const* b, double2* const* x, int* iters, double* relres,
+                           bool refine)
+{
+    if (R < 1 || R > MULTI_RHS) {
+        set_error("sys_solve_multi: 1 to 8 right-hand sides");
+        return SIE_ERR_ARG;
+    }
+    sie_ctx* c = op->mesh->ctx;
+    cudaStream_t st = c->stream;
+    const int64_t n = op->mesh->h.ne + op->mesh->h.nt;
+    SIE_TRY(charge_weight(op));
+    SIE_TRY(multi_scratch(op));
+    double2 *tw[MULTI_RHS], *bw[MULTI_RHS];
+    for (int q = 0; q < R; q++) {
+        tw[q] = op->mscr + q * multi_stride(op);
+        bw[q] = tw[q] + n;
+    }
+    auto A = [&](int Rn, const double2* const* u, double2* const* v) {
+        for (int q = 0; q < Rn; q++) {
+            SIE_TRY(apply_sys_fast(op, u[q], v[q]));
+            SIE_TRY(weight_rows(op, v[q], v[q], false));
+        }
+        return SIE_OK;
+    };
+    auto Minv = [&](int Rn, const double2* const* u, double2* const* v) {
+        for (int q = 0; q < Rn; q++) SIE_TRY(weight_rows(op, u[q], tw[q], true));
+        return precond_sys_multi(op, Rn, tw, v);
+    };
+    for (int i = 2; i < 6; i++) op->stats[i] = 0;
+    if (op->gstat) SIE_CUDA_TRY(cudaMemsetAsync(op->gstat, 0, sizeof(double) * 2, st));
+    for (int q = 0; q < R; q++) SIE_TRY(weight_rows(op, b[q], bw[q], false));
+    int it[MULTI_RHS];
+    double rr[MULTI_RHS];
+    sie_status s = SIE_OK;
+    if (!refine) {
+        s = fgmres_multi(c, op->kmulti, R, n, A, Minv, bw, x, op->p.tol_outer, op->p.maxit, op->p.restart, it, rr);
+        if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
+    } else {
+        double2 *r[MULTI_RHS], *d[MULTI_RHS], *t[MULTI_RHS];
+        for (int q = 0; q < R; q++) {
+            r[q] = op->ir_multi + (int64_t)q * n;
+            d[q] = op->ir_multi + (int64_t)(MULTI_RHS + q) * n;
+            t[q] = op->ir_multi + (int64_t)(2 * MULTI_RHS + q) * n;
+            SIE_CUDA_TRY(cudaMemsetAsync(x[q], 0, sizeof(double2) * n, st));
+        }
+        KrylovWork& K0 = op->kmulti[0];
+        SIE_TRY(K0.alloc(st, n, op->p.restart));
+        double bn[MULTI_RHS], rel[MULTI_RHS], rel_prev = 1.0;
+        for (int q = 0; q < R; q++) SIE_TRY(norm2(st, n, bw[q], K0.part, K0.h, K0.resid_h, &bn[q]));
+        const int saved = op->p.precision;
+        const int SWEEPS = 10;
+        bool fp64_corr = false;
+        int total = 0;
+        for (int sweep = 0; sweep <= SWEEPS; sweep++) {
+            op->p.precision = SIE_FP64;
+            if (sweep > 0 && (s = A(R, x, t)) != SIE_OK) break;
+            double worst = 0;
+            for (int q = 0; q < R && s == SIE_OK; q++) {
+                SIE_CUDA_TRY(cudaMemcpyAsync(r[q], bw[q], sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+                if (sweep > 0) s = axpby(st, n, -1.0, t[q], 1.0, r[q]);
+                double rn = 0;
+                if (s == SIE_OK) s = norm2(st, n, r[q], K0.part, K0.h, K0.resid_h, &rn);
+                rel[q] = bn[q] > 0 ? rn / bn[q] : 0.0;
+                worst = std::max(worst, rel[q]);
+            }
+            if (s != SIE_OK) break;
+            if (worst < op->p.tol_outer || sweep == SWEEPS || total >= op->p.maxit) break;
+            if (sweep >= 2 && worst > 0.5 * rel_prev) fp64_corr = true;
+            rel_prev = worst;
+            op->p.precision = fp64_corr ? SIE_FP64 : SIE_MIXED;
+            const double tc = std::min(1e-2, std::max(1e-6, 0.5 * op->p.tol_outer / worst));
+            int itc[MULTI_RHS];
+            double rrc[MULTI_RHS];
+            s = fgmres_multi(c, op->kmulti, R, n, A, Minv, r, d, tc, op->p.maxit - total, op->p.restart, itc, rrc);
+            total += itc[0];
+            if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) break;
+            s = SIE_OK;
+            for (int q = 0; q < R && s == SIE_OK; q++) s = axpby(st, n, 1.0, d[q], 1.0, x[q]);
+            if (s != SIE_OK) break;
+        }
+        op->p.precision = saved;
+        if (s != SIE_OK) return s;
+        for (int q = 0; q < R; q++) {
+            it[q] = total;
+            rr[q] = rel[q];
+        }
+        s = SIE_OK;
+        for (int q = 0; q < R; q++)
+            if (!(rr[q] < op->p.tol_outer)) s = SIE_ERR_NOT_CONVERGED;
+    }
+    double itmax = 0, rrmax = 0;
+    for (int q = 0; q < R; q++) {
+        if (iters) iters[q] = it[q];
+        if (relres) relres[q] = rr[q];
+        itmax = std::max(itmax, (double)it[q]);
+        rrmax = std::max(rrmax, rr[q]);
+    }
+    op->stats[0] = itmax;
+    op->stats[1] = rrmax;
+    if (s == SIE_OK) s = nested_check(op, "sie_solve");
+    if (s == SIE_OK || s == SIE_ERR_NOT_CONVERGED) SIE_TRY(constraint_lu_check(op));
+    return s;
 }
 
 // k0^2 eta0^2 / (4 pi): sigma = scale |N_perp(H) + rhat x N(E')|^2

@@ -17,6 +17,12 @@ materials and frequencies admitted into concurrent slots.
   context of the slot that built it; a request that uses it holds that
   context's lock (calls on one context never overlap), and a key being built
   makes the other requests for it wait instead of building it again.
+* Cross-request batching: when a slot is about to solve on an operator, it
+  takes every queued request of the same operator whose plane waves still
+  fit in max_batch_rhs (8) together with its own, and solves all of them as
+  one several-right-hand-side solve: lockstep blocks whose iterations apply
+  the system product and the constraint preconditioner to all of the
+  block's vectors at once (the dense factorisation is read once for them).
 * Device memory: before a slot builds an operator it needs free device memory
   of at least the reserve (10% of the device by default) plus an estimate of
   the operator's size (bytes per RWG unknown: the median of the ratios
@@ -41,17 +47,26 @@ import numpy as np
 
 
 class Request:
-    """One scattering solve.  params: extra sie_params fields (e.g. tol_outer)."""
+    """One scattering solve.  khat, epol: one plane wave (3,) or several (k, 3)
+    -- each is one right-hand side of the same operator; the answer's rcs is
+    then (k, ndir).  params: extra sie_params fields (e.g. tol_outer)."""
 
     def __init__(self, V, T, freq, eps_r, sigma, khat, epol, rhat, params=None):
         self.V = np.ascontiguousarray(V, dtype=np.float64)
         self.T = np.ascontiguousarray(T, dtype=np.int32)
         self.freq, self.eps_r, self.sigma = float(freq), float(eps_r), float(sigma)
-        self.khat = np.asarray(khat, float)
-        self.epol = np.asarray(epol, float)
+        self.single = np.ndim(khat) == 1
+        self.khat = np.atleast_2d(np.asarray(khat, float))
+        self.epol = np.atleast_2d(np.asarray(epol, float))
+        if self.khat.shape != self.epol.shape or self.khat.shape[1] != 3:
+            raise ValueError("khat and epol: (3,) or (k, 3) each, the same shape")
         self.rhat = np.atleast_2d(np.asarray(rhat, float))
         self.params = dict(params or {})
         self.ne = 3 * len(self.T) // 2
+
+    @property
+    def nrhs(self):
+        return len(self.khat)
 
     def key(self):
         """Operators are shared by requests with the same mesh, frequency,
@@ -85,11 +100,35 @@ class LibraryBackend:
         return (mesh, op)
 
     def run(self, handle, req):
+        return self.run_batch(handle, [req])[0]
+
+    def run_batch(self, handle, reqs):
+        """All plane waves of reqs (requests of one operator) as one
+        several-right-hand-side solve: lockstep blocks of 8, so the product
+        and the preconditioner of an iteration serve every request of the
+        block together."""
         _, op = handle
-        b = op.rhs_planewave(req.khat, req.epol)
-        x, it, rr = op.solve(b, check=False)
-        rcs = op.rcs(x, req.rhat)
-        return {"rcs": rcs, "iters": int(it[0]), "relres": float(rr[0])}
+        n = op.mesh.ne + op.mesh.nt
+        k = sum(r.nrhs for r in reqs)
+        B = np.zeros((k, n), np.complex128)
+        i = 0
+        for r in reqs:
+            for kh, ep in zip(r.khat, r.epol):
+                op.rhs_planewave(kh, ep, out=B[i])
+                i += 1
+        X, it, rr = op.solve(B if k > 1 else B[0], nrhs=k, check=False)
+        X = X.reshape(k, n)
+        outs, i = [], 0
+        for r in reqs:
+            rcs = np.stack([op.rcs(X[i + q], r.rhat) for q in range(r.nrhs)])
+            its = [int(v) for v in it[i:i + r.nrhs]]
+            res = [float(v) for v in rr[i:i + r.nrhs]]
+            i += r.nrhs
+            if r.single:
+                outs.append({"rcs": rcs[0], "iters": its[0], "relres": res[0], "batch_rhs": k})
+            else:
+                outs.append({"rcs": rcs, "iters": its, "relres": res, "batch_rhs": k})
+        return outs
 
     def release(self, handle):
         mesh, op = handle
@@ -109,11 +148,12 @@ class Server:
     """Slots, queue, one shared operator cache and memory admission (module docstring)."""
 
     def __init__(self, slots=2, backend_factory=None, reserve_fraction=0.10, bytes_per_unknown=128 * 1024,
-                 wait_s=0.05):
+                 wait_s=0.05, max_batch_rhs=8):
         self.backend_factory = backend_factory or (lambda slot: LibraryBackend(0))
         self.reserve_fraction = reserve_fraction
         self.bytes_per_unknown = float(bytes_per_unknown)   # estimate until builds are measured
         self.wait_s = wait_s
+        self.max_batch_rhs = int(max_batch_rhs)
         self._cv = threading.Condition()
         self._queue = collections.deque()
         self._busy = 0
@@ -198,27 +238,60 @@ class Server:
                     break
                 req, fut, t0 = self._queue.popleft()
                 self._busy += 1
+            batch = [(req, fut, t0)]
             try:
                 if fut.set_running_or_notify_cancel():
-                    out = self._serve(slot, req)
-                    with self._cv:
-                        self._lat.append(time.perf_counter() - t0)
-                    fut.set_result(out)
+                    self._serve(slot, batch)
             except BaseException as e:
-                if not fut.done():
-                    fut.set_exception(e)
+                for _, f, _ in batch:
+                    if not f.done():
+                        f.set_exception(e)
             finally:
                 with self._cv:
                     self._busy -= 1
                     self._cv.notify_all()
 
+    def _take_same_key(self, key, batch):
+        """Cross-request batching: move queued requests of the operator `key`
+        into batch while its right-hand sides fit in max_batch_rhs (called
+        with self._cv held)."""
+        have = sum(r.nrhs for r, _, _ in batch)
+        keep = collections.deque()
+        while self._queue:
+            item = self._queue.popleft()
+            r, f, _ = item
+            if r.key() == key and have + r.nrhs <= self.max_batch_rhs:
+                if f.set_running_or_notify_cancel():
+                    batch.append(item)
+                    have += r.nrhs
+                    self.counters["batched"] += 1
+            else:
+                keep.append(item)
+        self._queue = keep
+
+    def _finish(self, batch, outs, slot):
+        now = time.perf_counter()
+        for (_, f, t0), out in zip(batch, outs):
+            out["slot"] = slot
+            with self._cv:
+                self._lat.append(now - t0)
+            f.set_result(out)
+
+    def _run(self, backend, handle, batch):
+        reqs = [r for r, _, _ in batch]
+        if len(reqs) > 1 and hasattr(backend, "run_batch"):
+            return backend.run_batch(handle, reqs)
+        return [backend.run(handle, r) for r in reqs]
+
     def _count(self, name):
         with self._cv:
             self.counters[name] += 1
 
-    def _serve(self, slot, req):
-        """Run req on the cached operator of its key (built here, in this
-        slot's context, if no slot has it)."""
+    def _serve(self, slot, batch):
+        """Run the batch (its first request, plus queued requests of the same
+        operator taken just before the solve) on the cached operator of the
+        key (built here, in this slot's context, if no slot has it)."""
+        req = batch[0][0]
         key = req.key()
         while True:
             with self._cv:
@@ -236,10 +309,10 @@ class Server:
                     if still:
                         self._cache.move_to_end(key)
                         self.counters["reused"] += 1
+                        self._take_same_key(key, batch)
                 if still:
-                    out = self._backends[owner].run(handle, req)
-                    out["slot"] = slot
-                    return out
+                    self._finish(batch, self._run(self._backends[owner], handle, batch), slot)
+                    return
             # evicted between the look-up and the lock: look again
         try:
             with self._ctx_locks[slot]:
@@ -247,9 +320,8 @@ class Server:
                 with self._cv:
                     self._cache[key] = (handle, slot)
                     self.counters["built"] += 1
-                out = self._backends[slot].run(handle, req)
-                out["slot"] = slot
-                return out
+                    self._take_same_key(key, batch)
+                self._finish(batch, self._run(self._backends[slot], handle, batch), slot)
         finally:
             with self._cv:
                 self._building.discard(key)

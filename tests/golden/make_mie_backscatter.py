@@ -1,5 +1,10 @@
 """Writes mie_backscatter.txt: the Mie-series monostatic RCS of the spheres the
-benchmark solves (the Sec. V-A check), from oracle/mie.py only.
+benchmark solves (the Sec. V-A check), from oracle/mie.py only.  Besides the
+two workload spheres it draws (seed 5) the operator catalogue of the
+benchmark's serving trace: spheres meshed at level 2 or 3 with
+f log-uniform in [0.1, 100] GHz, k0 r uniform in [0.2, 1], sigma
+log-uniform in [1e-2, 5.8e7] S/m and eps_r uniform in [1, 12] (the serving
+configuration's material and frequency ranges on electrically small spheres).
 
     python tests/golden/make_mie_backscatter.py
 """
@@ -18,8 +23,22 @@ SPHERES = [
 ]
 
 
+def serve_catalogue(k=6, seed=5):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(k):
+        f = 10 ** rng.uniform(8, 11)
+        kr = rng.uniform(0.2, 1.0)
+        a = kr * 299792458.0 / (2 * np.pi * f)
+        sigma = 10 ** rng.uniform(-2, np.log10(5.8e7))
+        er = rng.uniform(1, 12)
+        out.append((f"serve-{i}-L{2 + i % 2}", float(a), float(f), float(er), float(sigma)))
+    return out
+
+
 def rows():
-    for name, a, f, er, s in SPHERES:
+    for name, a, f, er, s in SPHERES + serve_catalogue():
         yield name, a, f, er, s, mie.backscatter_rcs(a, f, er, s)
 
 
@@ -28,7 +47,7 @@ def main():
         fh.write("# Mie-series backscatter RCS (m^2), written by make_mie_backscatter.py (oracle/mie.py)\n")
         fh.write("# name radius_m freq_hz eps_r sigma_S_per_m rcs_m2\n")
         for r in rows():
-            fh.write("%s %.6e %.6e %.6e %.6e %.17e\n" % r)
+            fh.write("%s %.17e %.17e %.17e %.17e %.17e\n" % r)
 
 
 if __name__ == "__main__":

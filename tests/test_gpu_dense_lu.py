@@ -54,6 +54,22 @@ def test_dense_solve_large(lib, inverse):
     assert np.linalg.norm(r) <= 2e-5 * np.linalg.norm(A, 2) * np.linalg.norm(x)
 
 
+@pytest.mark.parametrize("inverse", [False, True], ids=["triangular", "inverse"])
+@pytest.mark.parametrize("n", [257, 1000])
+def test_dense_solve_several_rhs(lib, n, inverse):
+    """11 right-hand sides (a block of 8 through one pass over the inverse,
+    then 3; odd n falls back to one product per right-hand side): each equals
+    LAPACK's solve."""
+    A, _ = _rand(n, 21)
+    A = A + 4.0 * np.sqrt(n) * np.eye(n)
+    rng = np.random.default_rng(22)
+    B = rng.standard_normal((11, n)) + 1j * rng.standard_normal((11, n))
+    X = lib.dense_solve(A, B, inverse=inverse)
+    ref = np.linalg.solve(A, B.T).T
+    for q in range(11):
+        assert np.linalg.norm(X[q] - ref[q]) <= 2e-4 * np.linalg.norm(ref[q])
+
+
 def test_singular_matrix_is_an_error(lib):
     A, b = _rand(100, 2)
     A[:, 17] = 0.0
@@ -63,10 +79,11 @@ def test_singular_matrix_is_an_error(lib):
 
 
 def test_constraint_lu_solves_like_the_iterative_path(lib, ctx):
-    """Dielectric sphere (320 triangles, AIM interior): with the dense LUs the
-    constraint preconditioners' triangle systems take a few GMRES iterations,
-    and the solve gives the same solution as with the iterative constraint
-    solve (dense_pc_max = 0), to the solver tolerances."""
+    """Dielectric sphere (320 triangles, AIM interior): with the dense LUs as
+    their preconditioners the constraint preconditioners' triangle systems take
+    a few GMRES iterations, and the solve gives the same solution as with the
+    plain iterative constraint solve (dense_pc_max = 0), to the solver
+    tolerances."""
     from synth import icosphere
     V, T = icosphere(2, 0.01, equal_volume=True)
     mesh = lib.Mesh(ctx, V, T)

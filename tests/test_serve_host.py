@@ -115,7 +115,8 @@ def test_operator_is_shared_across_slots():
         futs = [srv.submit(_req(100)) for _ in range(6)]
         outs = [f.result(timeout=30) for f in futs]
         st = srv.stats()
-    assert st["built"] == 1 and st["reused"] == 5
+    # requests queued while the operator is in use join that solve (batched)
+    assert st["built"] == 1 and st.get("reused", 0) + st.get("batched", 0) == 5
     assert all(o["iters"] == 1 for o in outs)
     assert dev.used == 0
 
@@ -138,3 +139,85 @@ def test_size_estimate_is_the_median():
         for f in (1e9, 2e9, 3e9):
             srv.submit(_req(100, freq=f)).result(timeout=30)
         assert srv.stats()["bytes_per_unknown"] == 2.0
+
+
+class BatchingBackend(FakeBackend):
+    """Records each batch it is given; answers per request."""
+
+    def __init__(self, dev, run_s=0.0):
+        super().__init__(dev, run_s)
+        self.batches = []
+
+    def run(self, handle, req):
+        return self.run_batch(handle, [req])[0]
+
+    def run_batch(self, handle, reqs):
+        time.sleep(self.run_s)
+        self.batches.append([r.khat[0, 0] for r in reqs])
+        return [{"rcs": np.array([r.khat[0, 0], r.nrhs]), "iters": 1, "relres": 0.0} for r in reqs]
+
+
+def _req_k(ne, freq, kx, nrhs=1):
+    V = np.zeros((3, 3))
+    T = np.zeros((2, 3), np.int32)
+    kh = [[kx, 0.0, -1.0]] * nrhs if nrhs > 1 else [kx, 0.0, -1.0]
+    ep = [[1.0, 0.0, 0.0]] * nrhs if nrhs > 1 else [1.0, 0.0, 0.0]
+    r = Request(V, T, freq, 1.0, 0.0, kh, ep, [[0, 0, 1]])
+    r.ne = ne
+    return r
+
+
+def test_queued_requests_of_one_operator_are_batched():
+    """One slot busy on another operator: the three requests queued meanwhile
+    for one operator are solved as one batch, each answered on its own; a
+    request of a third operator is not mixed in."""
+    dev = Device(10_000)
+    be = []
+
+    def factory(slot):
+        b = BatchingBackend(dev, run_s=0.2)
+        be.append(b)
+        return b
+
+    with Server(slots=1, backend_factory=factory, bytes_per_unknown=1) as srv:
+        first = srv.submit(_req_k(10, 1e9, 0.5))
+        time.sleep(0.05)
+        same = [srv.submit(_req_k(10, 2e9, 0.1 * (i + 1))) for i in range(3)]
+        other = srv.submit(_req_k(10, 3e9, 0.9))
+        out = [f.result(timeout=10) for f in same]
+        o = other.result(timeout=10)
+        first.result(timeout=10)
+        st = srv.stats()
+    for i, r in enumerate(out):
+        assert r["rcs"][0] == pytest.approx(0.1 * (i + 1))
+    assert o["rcs"][0] == pytest.approx(0.9)
+    assert st["batched"] == 2 and st["completed"] == 5
+    assert sorted(len(b) for b in be[0].batches) == [1, 1, 3]
+
+
+def test_batches_respect_the_right_hand_side_budget():
+    """Requests of 3 plane waves each with max_batch_rhs = 8: two per batch."""
+    dev = Device(10_000)
+    be = []
+
+    def factory(slot):
+        b = BatchingBackend(dev, run_s=0.1)
+        be.append(b)
+        return b
+
+    with Server(slots=1, backend_factory=factory, max_batch_rhs=8, bytes_per_unknown=1) as srv:
+        block = srv.submit(_req_k(10, 1e9, 0.5))
+        time.sleep(0.03)
+        futs = [srv.submit(_req_k(10, 2e9, 0.1 * (i + 1), nrhs=3)) for i in range(4)]
+        for f in futs:
+            f.result(timeout=10)
+        block.result(timeout=10)
+    assert sorted(len(b) for b in be[0].batches) == [1, 2, 2]
+
+
+def test_request_with_several_plane_waves():
+    r = _req_k(10, 1e9, 0.3, nrhs=4)
+    assert r.nrhs == 4 and not r.single
+    with pytest.raises(ValueError):
+        Request(np.zeros((3, 3)), np.zeros((2, 3), np.int32), 1e9, 1.0, 0.0, [[0, 0, 1], [0, 1, 0]], [1, 0, 0],
+                [[0, 0, 1]])
