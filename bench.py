@@ -322,7 +322,12 @@ def run_ours(args):
         block = block_stats(sie, op, ne, stream, args)
     solves = solve_stats(sie, ctx, args) if not args.no_solve else None
     lossy_solves = lossy_solve_stats(sie, op, args, wl) if not args.no_solve else None
-    serving = serving_stats(args) if (not args.no_solve and args.serve_requests > 0 and rank == 0) else None
+    serving = None
+    if not args.no_solve and args.serve_requests > 0 and rank == 0:
+        try:
+            serving = serving_stats(args)
+        except Exception as e:  # the trace's failure is reported, not fatal to the line
+            serving = {"error": f"{type(e).__name__}: {e}"[:300]}
     ms, e2e_s = combine_ranks(ms, e2e_s, world, f"cuda:{local}")
     if rank != 0:
         return
@@ -553,6 +558,32 @@ def lossy_solve_stats(sie, op, args, wl):
             "rcs_rel_err_vs_mie": errs, "last_solve_stats": op.stats()}
     if dirs:
         out["refined_vs_fp64"] = {"speedup": out["refined"]["solves_per_s"] / out["fp64"]["solves_per_s"]}
+    # one block of R right-hand sides solved in lockstep (sie_solve nrhs = R)
+    R = args.lockstep_rhs
+    if R > 1:
+        bdirs = []
+        for i in range(R):
+            z = rng.uniform(-1, 1)
+            ph = rng.uniform(0, 2 * np.pi)
+            kh = np.array([np.sqrt(1 - z * z) * np.cos(ph), np.sqrt(1 - z * z) * np.sin(ph), z])
+            ep = np.cross(kh, [0.3, -0.5, 0.8])
+            bdirs.append((kh, ep / np.linalg.norm(ep)))
+        B = np.stack([op.rhs_planewave(kh, ep) for kh, ep in bdirs])
+        for refine in (False, True):
+            t0 = time.perf_counter()
+            X, it, rr = op.solve(B, nrhs=R, check=False, refine=refine)
+            dt = time.perf_counter() - t0
+            errs = [float(op.rcs(X[q], -bdirs[q][0])[0] / ref - 1.0) for q in range(R)]
+            conv = [bool(v < op_tol(sie)) for v in rr]
+            out[("refined" if refine else "fp64") + "_lockstep"] = {
+                "rhs": R, "wall_s": dt, "solves_per_s": R / dt, "iters": int(it.max()),
+                "ok_solves": int(sum(c and abs(e) <= 0.01 for c, e in zip(conv, errs))),
+                "rcs_rel_err_vs_mie_max": float(np.abs(errs).max())}
+        if dirs:
+            out["refined_lockstep_vs_fp64"] = {
+                "speedup": out["refined_lockstep"]["solves_per_s"] / out["fp64"]["solves_per_s"],
+                "note": "solves/s of the mixed-precision refinement with lockstep blocks over the plain FP64 "
+                        "path solving one right-hand side at a time, same workload and tolerance"}
     return out
 
 
@@ -574,34 +605,41 @@ def serving_stats(args):
     args.serve_rate per second, each on one of the catalogue's operators
     (uniform) with 1 to 4 plane waves (backscatter), through the request
     loop (paper_2003_11679_gb300/serve.py: two slots, shared resident
-    operator cache, cross-request batching into lockstep solves).  Cold start:
-    the catalogue's operator builds fall in the trace.  Latency is per
-    request from its arrival; solves/s counts right-hand sides over the
-    trace's wall time; each solve's RCS is compared with the Mie series."""
+    operator cache, cross-request batching into lockstep solves).  Two traces
+    on one server: `cold` starts with an empty cache (the catalogue's operator
+    builds fall in the trace), `warm` follows with new arrivals on the
+    resident operators.  Latency is per request from its arrival; solves/s
+    counts right-hand sides over the trace's wall time; each solve's RCS is
+    compared with the Mie series."""
     from paper_2003_11679_gb300.serve import Request, Server
     from synth import icosphere
     cat = serve_catalogue()
     rng = np.random.default_rng(17)
     meshes = {c[0]: icosphere(c[5], c[1], equal_volume=True) for c in cat}
-    reqs, arrivals, t = [], [], 0.0
-    for i in range(args.serve_requests):
-        t += rng.exponential(1.0 / args.serve_rate)
-        c = cat[rng.integers(len(cat))]
-        k = int(rng.integers(1, 5))
-        khs, eps = [], []
-        for _ in range(k):
-            z = rng.uniform(-1, 1)
-            ph = rng.uniform(0, 2 * np.pi)
-            kh = np.array([np.sqrt(1 - z * z) * np.cos(ph), np.sqrt(1 - z * z) * np.sin(ph), z])
-            ep = np.cross(kh, [0.3, -0.5, 0.8])
-            khs.append(kh)
-            eps.append(ep / np.linalg.norm(ep))
-        V, T = meshes[c[0]]
-        r = Request(V, T, c[2], c[3], c[4], np.array(khs), np.array(eps), -np.array(khs))
-        reqs.append((r, c))
-        arrivals.append(t)
-    errs, res, nrhs = [], [], 0
-    with Server(slots=2) as srv:
+
+    def draw():
+        reqs, arrivals, t = [], [], 0.0
+        for i in range(args.serve_requests):
+            t += rng.exponential(1.0 / args.serve_rate)
+            c = cat[rng.integers(len(cat))]
+            k = int(rng.integers(1, 5))
+            khs, eps = [], []
+            for _ in range(k):
+                z = rng.uniform(-1, 1)
+                ph = rng.uniform(0, 2 * np.pi)
+                kh = np.array([np.sqrt(1 - z * z) * np.cos(ph), np.sqrt(1 - z * z) * np.sin(ph), z])
+                ep = np.cross(kh, [0.3, -0.5, 0.8])
+                khs.append(kh)
+                eps.append(ep / np.linalg.norm(ep))
+            V, T = meshes[c[0]]
+            reqs.append((Request(V, T, c[2], c[3], c[4], np.array(khs), np.array(eps), -np.array(khs)), c))
+            arrivals.append(t)
+        return reqs, arrivals
+
+    def trace(srv, reqs, arrivals):
+        before = dict(srv.counters)
+        nlat0 = len(srv._lat)
+        errs, res, nrhs, failed = [], [], 0, []
         t0 = time.perf_counter()
         futs = []
         for (r, c), ta in zip(reqs, arrivals):
@@ -610,24 +648,33 @@ def serving_stats(args):
                 time.sleep(dt)
             futs.append((srv.submit(r), r, c))
         for f, r, c in futs:
-            out = f.result(timeout=1800)
+            try:
+                out = f.result(timeout=1800)
+            except Exception as e:  # reported in the line, the trace goes on
+                failed.append(f"{c[0]}: {type(e).__name__}: {e}"[:200])
+                continue
             rcs = np.atleast_2d(out["rcs"])
             for q in range(r.nrhs):
                 errs.append(float(rcs[q, q] / c[6] - 1.0))  # backscatter: rhat_q = -khat_q
             res.extend(np.atleast_1d(out["relres"]).tolist())
             nrhs += r.nrhs
         wall = time.perf_counter() - t0
-        st = srv.stats()
-    tol = 1e-4
-    ae = np.abs(errs)
-    return {"requests": len(reqs), "rate_per_s": args.serve_rate, "slots": 2, "operators": len(cat),
-            "right_hand_sides": nrhs, "wall_s": wall, "solves_per_s": nrhs / wall, "p50_s": st.get("p50_s"),
-            "p99_s": st.get("p99_s"), "built": st.get("built", 0), "reused": st.get("reused", 0),
-            "batched": st.get("batched", 0), "converged": int(sum(v < tol for v in res)),
-            "rcs_rel_err_vs_mie_p50": float(np.median(ae)), "rcs_rel_err_vs_mie_max": float(ae.max()),
-            "within_1pct": int((ae <= 0.01).sum()), "within_5pct": int((ae <= 0.05).sum()),
-            "note": "cold start: operator builds inside the trace; catalogue = tests/golden/mie_backscatter.txt "
-                    "serve-* rows (spheres, level 2-3 meshes)"}
+        lat = np.array(srv._lat[nlat0:])
+        cnt = {k: srv.counters.get(k, 0) - before.get(k, 0) for k in ("built", "reused", "batched")}
+        ae = np.abs(errs) if errs else np.array([np.nan])
+        return {"requests": len(reqs), "right_hand_sides": nrhs, "wall_s": wall, "solves_per_s": nrhs / wall,
+                "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_s": float(np.percentile(lat, 99)) if len(lat) else None, **cnt,
+                "converged": int(sum(v < 1e-4 for v in res)),
+                "rcs_rel_err_vs_mie_p50": float(np.median(ae)), "rcs_rel_err_vs_mie_max": float(ae.max()),
+                "within_1pct": int((ae <= 0.01).sum()), "failed_requests": failed}
+
+    with Server(slots=2) as srv:
+        cold = trace(srv, *draw())
+        warm = trace(srv, *draw())
+    return {"rate_per_s": args.serve_rate, "slots": 2, "operators": len(cat), "cold": cold, "warm": warm,
+            "note": "catalogue = tests/golden/mie_backscatter.txt serve-* rows (spheres, level 2-3 meshes, "
+                    "the serving configuration's sigma, eps_r and frequency ranges)"}
 
 
 def op_tol(sie):
@@ -729,6 +776,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--solves", type=int, default=4)
     ap.add_argument("--lossy-solves", type=int, default=3)
+    ap.add_argument("--lockstep-rhs", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--interior", default="gibc", choices=["gibc", "sibc"],
