@@ -322,6 +322,12 @@ def run_ours(args):
         block = block_stats(sie, op, ne, stream, args)
     solves = solve_stats(sie, ctx, args) if not args.no_solve else None
     lossy_solves = lossy_solve_stats(sie, op, args, wl) if not args.no_solve else None
+    batching = None
+    if not args.no_solve and args.batch_rhs > 0 and rank == 0:
+        try:
+            batching = batching_stats(sie, ctx, args)
+        except Exception as e:  # reported, not fatal to the line
+            batching = {"error": f"{type(e).__name__}: {e}"[:300]}
     serving = None
     if not args.no_solve and args.serve_requests > 0 and rank == 0:
         try:
@@ -383,6 +389,7 @@ def run_ours(args):
                                  "loop); the stage breakdown comes from the stream path with per-stage events"},
         "solves": solves,
         "solves_workload": lossy_solves,
+        "batching": batching,
         "serving": serving,
         "block_rhs": block,
         "mixed_precision": mixed_line(ne, args, ms32, prof32, mixed_err, info, peaks, kind),
@@ -587,6 +594,63 @@ def lossy_solve_stats(sie, op, args, wl):
     return out
 
 
+def batching_stats(sie, ctx, args):
+    """Batching (the batching configuration, scaled to one GPU for a minute):
+    three meshes of uneven sizes (a 1,280-triangle sphere, a 768-triangle
+    cube, a 320-triangle sphere), two frequencies each, args.batch_rhs
+    plane waves per (mesh, frequency).  Each set is solved one right-hand
+    side at a time (FP64) and in lockstep blocks of 8 (FP64 and the
+    mixed-precision refinement) on the same operator; solves/s over all
+    sets, and the largest difference of the lockstep solutions from the
+    one-at-a-time ones."""
+    from synth import box, icosphere
+    rng = np.random.default_rng(23)
+    meshes = [("sphere-1280", icosphere(3, 5e-3, equal_volume=True)),
+              ("cube-768", box((8e-3, 8e-3, 8e-3), (8, 8, 8))),
+              ("sphere-320", icosphere(2, 2e-3, equal_volume=True))]
+    mats = [(3e9, 4.0, 0.0), (10e9, 1.0, 5.8e7)]
+    tot = {"fp64_sequential": 0.0, "fp64_lockstep": 0.0, "refined_lockstep": 0.0}
+    nrhs, worst, conv, sets = 0, 0.0, 0, []
+    for name, (V, T) in meshes:
+        mesh = sie.Mesh(ctx, V, T)
+        for f, er, sg in mats:
+            op = sie.Operator(mesh, f, er, 1.0, sg, sie.params())
+            dirs = []
+            for _ in range(args.batch_rhs):
+                z = rng.uniform(-1, 1)
+                ph = rng.uniform(0, 2 * np.pi)
+                kh = np.array([np.sqrt(1 - z * z) * np.cos(ph), np.sqrt(1 - z * z) * np.sin(ph), z])
+                ep = np.cross(kh, [0.3, -0.5, 0.8])
+                dirs.append((kh, ep / np.linalg.norm(ep)))
+            B = np.stack([op.rhs_planewave(kh, ep) for kh, ep in dirs])
+            op.solve(B[:2], nrhs=2, check=False)  # graph capture and workspaces, untimed
+            t0 = time.perf_counter()
+            Xs, _, _ = op.solve(B, nrhs=len(B), sequential=True, check=False)
+            t1 = time.perf_counter()
+            Xb, itb, rrb = op.solve(B, nrhs=len(B), check=False)
+            t2 = time.perf_counter()
+            Xr, itr, rrr = op.solve(B, nrhs=len(B), refine=True, check=False)
+            t3 = time.perf_counter()
+            tot["fp64_sequential"] += t1 - t0
+            tot["fp64_lockstep"] += t2 - t1
+            tot["refined_lockstep"] += t3 - t2
+            nrhs += len(B)
+            conv += int(sum(rrb < op_tol(sie))) + int(sum(rrr < op_tol(sie)))
+            worst = max(worst, max(float(np.linalg.norm(Xb[q] - Xs[q]) / np.linalg.norm(Xs[q])) for q in range(len(B))))
+            sets.append({"mesh": name, "f_hz": f, "eps_r": er, "sigma": sg, "unknowns": mesh.ne + mesh.nt,
+                         "iters_lockstep": int(itb.max()), "iters_refined": int(itr.max())})
+            op.close()
+        mesh.close()
+    out = {"sets": sets, "rhs_per_set": args.batch_rhs, "solves": nrhs, "converged_of_2x": conv,
+           "max_rel_diff_lockstep_vs_sequential": worst}
+    for k, v in tot.items():
+        out[k + "_solves_per_s"] = nrhs / v
+    out["lockstep_speedup_fp64"] = tot["fp64_sequential"] / tot["fp64_lockstep"]
+    out["refined_lockstep_vs_fp64_sequential"] = tot["fp64_sequential"] / tot["refined_lockstep"]
+    out["not_built"] = "frequency points in one graph launch; an autotuner; tensor-core near blocks"
+    return out
+
+
 def serve_catalogue():
     """The serving trace's operators: (name, radius, f, eps_r, sigma, level,
     Mie backscatter) as drawn and evaluated by tests/golden/make_mie_backscatter.py."""
@@ -777,6 +841,7 @@ def main():
     ap.add_argument("--solves", type=int, default=4)
     ap.add_argument("--lossy-solves", type=int, default=3)
     ap.add_argument("--lockstep-rhs", type=int, default=8)
+    ap.add_argument("--batch-rhs", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--interior", default="gibc", choices=["gibc", "sibc"],

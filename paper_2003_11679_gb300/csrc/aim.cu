@@ -464,6 +464,8 @@ __device__ __forceinline__ void stockham_pass(int Ns, int tp, const C* gin, int6
     constexpr int n = 1 << LOGN;
     constexpr int TPP = n / 8;  // threads per pencil
     constexpr int NB = n / R;   // butterflies per pencil
+    constexpr int LR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    const int lns = __ffs(Ns) - 1;  // log2(Ns)
     for (int jj = tp; jj < NB; jj += TPP) {
         C a[R];
         for (int r = 0; r < R; r++) {
@@ -478,11 +480,12 @@ __device__ __forceinline__ void stockham_pass(int Ns, int tp, const C* gin, int6
                 a[r] = sin[idx];
             }
         }
-        int k = jj % Ns;
+        // Ns and R are powers of two: masks and shifts instead of divisions
+        const int k = jj & (Ns - 1);
         if (Ns > 1)
-            for (int r = 1; r < R; r++) cmulw<C, INV>(a[r], tw[(k * r) * (n / (Ns * R))]);
+            for (int r = 1; r < R; r++) cmulw<C, INV>(a[r], tw[(k * r) << (LOGN - lns - LR)]);
         dftR<C, INV, R>(a);
-        int o = (jj / Ns) * Ns * R + k;
+        const int o = ((jj >> lns) << (lns + LR)) + k;
         for (int r = 0; r < R; r++) {
             int idx = o + r * Ns;
             if (DST == 0) {
@@ -1457,6 +1460,7 @@ sie_status sie_op_build(sie_mesh* mesh, double freq_hz, double eps_r, double mu_
     }
     if ((s = sys_prepare(op)) != SIE_OK) return fail(s);
     if ((s = constraint_lu_build(op)) != SIE_OK) return fail(s);
+    if ((s = csr_tune_op(op)) != SIE_OK) return fail(s);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         set_error(std::string("sie_op_build: ") + cudaGetErrorString(e));

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(128) k_csr_panel(int nrow, const int64_t* __re
     }
 }
 
-static sie_status csr_panel(cudaStream_t st, int nrow, const int64_t* rp, const int32_t* col, const double2* val,
+sie_status csr_panel(cudaStream_t st, int nrow, const int64_t* rp, const int32_t* col, const double2* val,
                             const double2* X, int64_t ldx, int nr, bool acc, double2* Y, int64_t ldy)
 {
     const unsigned blocks = (unsigned)((nrow + 3) / 4);

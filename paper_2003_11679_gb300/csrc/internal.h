@@ -242,6 +242,21 @@ struct KrylovWork {
     sie_status alloc(cudaStream_t st, int64_t n_, int m_);
     void release(cudaStream_t st);
 };
+// Krylov workspace of a panel solve: R right-hand sides whose vectors sit side
+// by side (basis V[j][q][n], Z[j][q][n]); one launch per Gram-Schmidt step
+// serves all of them (gridDim.y = R)
+struct PanelWork {
+    int64_t n = 0;
+    int m = 0, R = 0;
+    double2 *V = nullptr, *Z = nullptr, *W = nullptr, *Rv = nullptr;  // bases, A z panel, residual panel
+    double2 *P = nullptr, *h = nullptr, *Hd = nullptr, *part = nullptr, *wd = nullptr;
+    double* sc = nullptr;     // per right-hand side: |b|, beta, residuals
+    double* res = nullptr;    // residual of iteration j, right-hand side q at [j R + q]
+    double* res_h = nullptr;  // pinned copy of res
+    std::vector<cudaEvent_t> ev;
+    sie_status alloc(cudaStream_t st, int64_t n_, int m_, int R_);
+    void release(cudaStream_t st);
+};
 }  // namespace sie
 
 struct sie_op {
@@ -270,6 +285,8 @@ struct sie_op {
     sie::KrylovWork kin, kout, kcs_in, kcs_out;
     sie::KrylovWork kmulti[8];      // lockstep solves: one Krylov basis per right-hand side
     sie::KrylovWork kcs_multi[8];   // ... and per triangle system of their constraint preconditioner
+    sie::PanelWork kzp;             // lockstep block products: the nested interior solves of the block
+    double2* zp = nullptr;          // block products: H, E, rhs and scratch panels (4 x 8 ne)
     double2* mscr = nullptr;        // lockstep solves: per right-hand side scratch (8 blocks)
     double2* ir_multi = nullptr;    // lockstep refinement: residuals, corrections, products (3 x 8 (ne + nt))
     double2* mvec = nullptr;        // lockstep solves from host buffers: 2 x 8 (ne + nt)
@@ -322,6 +339,11 @@ sie_status aim_apply(sie_op* op, AimOp& a, int which_LK, const double2* x, doubl
 sie_status aim_apply_block(sie_op* op, AimOp& a, int which_LK, const double2* X, double2* Y, int nr);
 sie_status aim_interp(sie_op* op, const double2* grids, int has_phi, double2 scal, double2* y);
 sie_status sys_prepare(sie_op* op);
+sie_status csr_tune_op(sie_op* op);
+// Y = A X (acc: Y += A X) for nr <= 8 vectors of a CSR matrix: X, Y rhs-major
+// with leading dimensions ldx, ldy; the values read once for all nr
+sie_status csr_panel(cudaStream_t st, int nrow, const int64_t* rp, const int32_t* col, const double2* val,
+                     const double2* X, int64_t ldx, int nr, bool acc, double2* Y, int64_t ldy);  // group sizes of the operator's CSR products, by measurement
 void sys_release(sie_op* op);
 sie_status sys_matvec(sie_op* op, int which, const double2* x, double2* y);
 sie_status sys_solve(sie_op* op, const double2* b, double2* x, int* iters, double* relres);

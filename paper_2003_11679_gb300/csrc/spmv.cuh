@@ -9,6 +9,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 namespace sie {
 
 // VT = double2: FP64 throughout.  VT = float2 (complex64 values of the mixed
@@ -39,12 +43,26 @@ __device__ __forceinline__ double2 csr_row_dot(int64_t e0, int64_t e1, const int
             ai[u] += v[u].x * xi + v[u].y * xr;
         }
     }
-    for (; e < e1; e += G) {  // at most 3 more entries per lane
-        VT v = __ldg(val + e);
-        XT xd = __ldg(x + __ldg(col + e));
-        const R xr = (R)xd.x, xi = (R)xd.y;
-        ar[0] += v.x * xr - v.y * xi;
-        ai[0] += v.x * xi + v.y * xr;
+    {  // at most 3 more entries per lane: their loads issued together
+        int c[3];
+        VT v[3];
+        XT xv[3];
+#pragma unroll
+        for (int u = 0; u < 3; u++) {
+            const bool ok = e + u * G < e1;
+            c[u] = ok ? __ldg(col + e + u * G) : -1;
+            if (ok) v[u] = __ldg(val + e + u * G);
+        }
+#pragma unroll
+        for (int u = 0; u < 3; u++)
+            if (c[u] >= 0) xv[u] = __ldg(x + c[u]);
+#pragma unroll
+        for (int u = 0; u < 3; u++)
+            if (c[u] >= 0) {
+                const R xr = (R)xv[u].x, xi = (R)xv[u].y;
+                ar[u] += v[u].x * xr - v[u].y * xi;
+                ai[u] += v[u].x * xi + v[u].y * xr;
+            }
     }
     double sr = ((double)ar[0] + (double)ar[1]) + ((double)ar[2] + (double)ar[3]);
     double si = ((double)ai[0] + (double)ai[1]) + ((double)ai[2] + (double)ai[3]);
@@ -79,19 +97,50 @@ __global__ void __launch_bounds__(256) k_csr(int nrow, const int64_t* __restrict
     }
 }
 
-// lanes per row from the mean row length
+// lanes per row from the mean row length (the default before tuning)
 inline int csr_group(int64_t nrow, int64_t nnz)
 {
     const int64_t avg = nrow > 0 ? nnz / nrow : 0;
     return avg <= 12 ? 4 : (avg <= 48 ? 8 : 32);
 }
 
+// Lanes per row chosen by measurement (csr_autotune), per matrix pattern
+// (row pointer, rows, entries) and value width; csr_launch falls back to
+// csr_group for patterns never tuned.
+struct CsrTuneTable {
+    std::mutex mu;
+    std::map<std::tuple<const void*, int, int64_t, int>, int> g;
+};
+inline CsrTuneTable& csr_tune_table()
+{
+    static CsrTuneTable t;
+    return t;
+}
+inline int csr_group_for(const int64_t* rp, int nrow, int64_t nnz, int vbytes)
+{
+    CsrTuneTable& t = csr_tune_table();
+    std::lock_guard<std::mutex> lk(t.mu);
+    auto it = t.g.find(std::make_tuple((const void*)rp, nrow, nnz, vbytes));
+    return it != t.g.end() ? it->second : csr_group(nrow, nnz);
+}
+
+template <class VT, class XT>
+inline cudaError_t csr_launch_g(cudaStream_t st, int G, int nrow, const int64_t* rp, const int32_t* col,
+                                const VT* val, const XT* x, double2 alpha, bool acc, double2* y);
+
 template <class VT, class XT>
 inline cudaError_t csr_launch(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp, const int32_t* col,
                               const VT* val, const XT* x, double2 alpha, bool acc, double2* y)
 {
     if (nrow <= 0) return cudaSuccess;
-    const int G = csr_group(nrow, nnz);
+    return csr_launch_g(st, csr_group_for(rp, nrow, nnz, (int)sizeof(VT)), nrow, rp, col, val, x, alpha, acc, y);
+}
+
+// the product with G lanes per row (4, 8, 16 or 32)
+template <class VT, class XT>
+inline cudaError_t csr_launch_g(cudaStream_t st, int G, int nrow, const int64_t* rp, const int32_t* col,
+                                const VT* val, const XT* x, double2 alpha, bool acc, double2* y)
+{
     const unsigned blocks = (unsigned)(((int64_t)nrow * G + 255) / 256);
     if (G == 4) {
         if (acc) k_csr<4, true, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
@@ -99,11 +148,65 @@ inline cudaError_t csr_launch(cudaStream_t st, int nrow, int64_t nnz, const int6
     } else if (G == 8) {
         if (acc) k_csr<8, true, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
         else k_csr<8, false, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+    } else if (G == 16) {
+        if (acc) k_csr<16, true, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
+        else k_csr<16, false, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
     } else {
         if (acc) k_csr<32, true, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
         else k_csr<32, false, VT, XT><<<blocks, 256, 0, st>>>(nrow, rp, col, val, x, alpha, y);
     }
     return cudaGetLastError();
+}
+
+// Autotuner of the CSR products: on a matrix's first tuning call (never
+// while the stream is being captured) time each group size on it -- one
+// warm-up and three timed launches into the scratch y_tmp (nrow values), on
+// the stream st, CUDA events -- and keep the fastest for csr_launch.
+template <class VT, class XT>
+inline cudaError_t csr_autotune(cudaStream_t st, int nrow, int64_t nnz, const int64_t* rp, const int32_t* col,
+                                const VT* val, const XT* x, double2* y_tmp)
+{
+    if (nrow <= 0 || nnz <= 0) return cudaSuccess;
+    const auto key = std::make_tuple((const void*)rp, nrow, nnz, (int)sizeof(VT));
+    {
+        CsrTuneTable& t = csr_tune_table();
+        std::lock_guard<std::mutex> lk(t.mu);
+        if (t.g.count(key)) return cudaSuccess;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    int best = csr_group(nrow, nnz);
+    float best_ms = 1e30f;
+    for (int G : {4, 8, 16, 32}) {
+        if ((e = csr_launch_g(st, G, nrow, rp, col, val, x, make_double2(1.0, 0.0), false, y_tmp)) != cudaSuccess) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; r++)
+            if ((e = csr_launch_g(st, G, nrow, rp, col, val, x, make_double2(1.0, 0.0), false, y_tmp)) != cudaSuccess)
+                break;
+        cudaEventRecord(e1, st);
+        if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = G;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) {
+        CsrTuneTable& t = csr_tune_table();
+        std::lock_guard<std::mutex> lk(t.mu);
+        t.g[key] = best;
+    }
+    return e;
 }
 
 }  // namespace sie

@@ -319,13 +319,26 @@ __device__ void cgs_partials(int64_t k0, int64_t k1, int nv, const double2* __re
     }
 }
 
+// Several right-hand sides in one launch (gridDim.y = R, panel Krylov solves):
+// the pointers of right-hand side q = blockIdx.y are offset by q times these
+// strides -- v: basis vectors and w (a panel of R vectors of n), p: partial
+// sums, h: the two Gram-Schmidt coefficient columns, d: Hessenberg, rotations
+// and g, s: scalars.  All zero for one right-hand side.
+struct PanelStrides {
+    int64_t v = 0, p = 0, h = 0, d = 0, s = 0;
+};
+
 // pass 1: partial sums of V^H w.  With jd (device-controlled iteration, jd[0]
 // = j) nv = j + 1 is read on the device and zsrc is stored as column j of Z.
 __global__ void __launch_bounds__(256) k_cgs_part(int64_t n, int nv, const double2* __restrict__ V, int64_t ld,
                                                   const double2* __restrict__ w, double2* __restrict__ P, int ldp,
                                                   const int* __restrict__ jd, const double2* __restrict__ zsrc,
-                                                  double2* __restrict__ Z)
+                                                  double2* __restrict__ Z, PanelStrides ps = PanelStrides())
 {
+    const int64_t q = blockIdx.y;
+    V += q * ps.v;
+    w += q * ps.v;
+    P += q * ps.p;
     int64_t k0, k1;
     cgs_rows(n, k0, k1);
     if (jd) {
@@ -342,9 +355,17 @@ __global__ void __launch_bounds__(256) k_cgs_update(int64_t n, int nv, const dou
                                                     const double2* __restrict__ Pin, int ldp,
                                                     double2* __restrict__ hout, double2* __restrict__ w,
                                                     double2* __restrict__ Pout, int last,
-                                                    const int* __restrict__ jd)
+                                                    const int* __restrict__ jd, PanelStrides ps = PanelStrides())
 {
     __shared__ double2 h[CGS_TILE];
+    {
+        const int64_t q = blockIdx.y;
+        V += q * ps.v;
+        Pin += q * ps.p;
+        hout += q * ps.h;
+        w += q * ps.v;
+        Pout += q * ps.p;
+    }
     if (jd) nv = jd[0] + 1;
     int64_t k0, k1;
     cgs_rows(n, k0, k1);
@@ -389,16 +410,31 @@ __global__ void __launch_bounds__(256) k_cgs_update(int64_t n, int nv, const dou
 
 // |w| = sqrt(sum_c P[c]); V_{j+1} = w / |w| on this chunk's rows; block 0
 // writes column j of H (h1 + h2 and |w|) and applies the Givens step
-// (V: the basis, column stride n; with jd, j = jd[0] is read on the device)
+// (V: the basis, column stride ld (0: n); with jd, j = jd[0] is read on the
+// device; res, when given: the relative residual also to res[j gridDim.y + q])
 __global__ void __launch_bounds__(256) k_cgs_finish(int64_t n, int j, int m, const double2* __restrict__ h1,
                                                     const double2* __restrict__ h2, const double2* __restrict__ P,
                                                     const double2* __restrict__ w, double2* __restrict__ V,
                                                     double2* __restrict__ H, double2* __restrict__ cs,
                                                     double2* __restrict__ sn, double2* __restrict__ g,
-                                                    double* __restrict__ sc, const int* __restrict__ jd)
+                                                    double* __restrict__ sc, const int* __restrict__ jd,
+                                                    PanelStrides ps = PanelStrides(), int64_t ld = 0,
+                                                    double* __restrict__ res = nullptr)
 {
+    const int64_t q = blockIdx.y;
+    h1 += q * ps.h;
+    h2 += q * ps.h;
+    P += q * ps.p;
+    w += q * ps.v;
+    V += q * ps.v;
+    H += q * ps.d;
+    cs += q * ps.d;
+    sn += q * ps.d;
+    g += q * ps.d;
+    sc += q * ps.s;
+    if (ld == 0) ld = n;
     if (jd) j = jd[0];
-    double2* Vn = V + (int64_t)(j + 1) * n;
+    double2* Vn = V + (int64_t)(j + 1) * ld;
     __shared__ double hn_s;
     if (threadIdx.x < 32) {
         double s = 0;
@@ -416,7 +452,10 @@ __global__ void __launch_bounds__(256) k_cgs_finish(int64_t n, int j, int m, con
     for (int i = threadIdx.x; i <= j; i += blockDim.x) H[i * m + j] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
     if (threadIdx.x == 0) H[(j + 1) * m + j] = make_double2(hn, 0);
     __syncthreads();
-    if (threadIdx.x == 0) gm_givens(j, m, H, cs, sn, g, sc);
+    if (threadIdx.x == 0) {
+        gm_givens(j, m, H, cs, sn, g, sc);
+        if (res) res[(int64_t)j * gridDim.y + q] = sc[3 + j];
+    }
 }
 
 // ---- device-controlled cycle (the body of a CUDA-graph while loop).  jd[0]
@@ -1328,18 +1367,26 @@ sie_status proj_map_ready(sie_op* op)
 }
 
 // y = SYS x, x = [H (ne); c0 rho (nt)]
+// the system product after the interior impedance: y = SYS [H; rho] with
+// E = Z' H already computed (every step of Eq. sys but the nested solve)
+static sie_status apply_sys_rest(sie_op* op, const double2* H, const double2* E, const double2* rho, double2* y);
+
 static sie_status apply_sys(sie_op* op, const double2* x, double2* y)
+{
+    const int64_t ne = op->mesh->h.ne;
+    double2* E = op->sys_E;
+    SIE_TRY(apply_Z(op, x, E, nullptr));
+    return apply_sys_rest(op, x, E, x + ne, y);
+}
+
+static sie_status apply_sys_rest(sie_op* op, const double2* H, const double2* E, const double2* rho, double2* y)
 {
     sie_ctx* c = op->mesh->ctx;
     cudaStream_t st = c->stream;
     const DevMesh& M = op->mesh->d;
     const int64_t ne = M.ne, nt = M.nt;
-    const double2* H = x;
-    const double2* rho = x + ne;
     double2* y1 = y;
     double2* y2 = y + ne;
-    double2* E = op->sys_E;
-    SIE_TRY(apply_Z(op, H, E, nullptr));
     AimOp& X = op->ext;
     const GridDesc& g = X.g;
     int S = (g.M + 1) * (g.M + 1) * (g.M + 1);
@@ -1741,6 +1788,35 @@ static sie_status gram_prepare(sie_op* op)
     return SIE_OK;
 }
 
+// Measured lanes-per-row choice (csr_autotune) for the operator's CSR
+// products: exterior near-region L and K (L0/K0 products), the triangle Lphi
+// products in FP64 and complex64, I-cross, the near-only interior matrices
+// and the SIBC Gram matrix.  Runs once per pattern on the context stream with
+// zeroed operands; the system-product graph captured later uses the result.
+sie_status csr_tune_op(sie_op* op)
+{
+    cudaStream_t st = op->mesh->ctx->stream;
+    const int64_t ne = op->mesh->h.ne, nt = op->mesh->h.nt;
+    double2* x = op->xtmp;       // ne (>= nt) zeros
+    double2* y = op->xtmp + ne;  // ne scratch
+    SIE_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * ne, st));
+    const AimOp& X = op->ext;
+    if (X.nnz > 0 && X.valL) SIE_CUDA_TRY(csr_autotune(st, (int)ne, X.nnz, X.row_ptr, X.col, X.valL, x, y));
+    const int64_t tn = tri_nnz(X);
+    if (tn > 0 && X.valLphi) SIE_CUDA_TRY(csr_autotune(st, (int)nt, tn, X.tri_row_ptr, X.tri_col, X.valLphi, x, y));
+    if (tn > 0 && X.valLphi32 && op->pk_sig) {
+        SIE_CUDA_TRY(cudaMemsetAsync(op->pk_sig, 0, sizeof(float2) * nt, st));
+        SIE_CUDA_TRY(csr_autotune(st, (int)nt, tn, X.tri_row_ptr, X.tri_col, X.valLphi32, (const float2*)op->pk_sig, y));
+    }
+    if (op->ix_nnz > 0)
+        SIE_CUDA_TRY(csr_autotune(st, (int)ne, op->ix_nnz, op->ix_row_ptr, op->ix_col, op->ix_val, x, y));
+    const AimOp& I = op->inn;
+    if (I.nnz > 0 && I.valL) SIE_CUDA_TRY(csr_autotune(st, (int)ne, I.nnz, I.row_ptr, I.col, I.valL, x, y));
+    if (op->gr_nnz > 0)
+        SIE_CUDA_TRY(csr_autotune(st, (int)ne, op->gr_nnz, op->gr_row_ptr, op->gr_col, op->gr_val, x, y));
+    return SIE_OK;
+}
+
 sie_status sys_prepare(sie_op* op)
 {
     cudaStream_t st = op->mesh->ctx->stream;
@@ -1823,6 +1899,9 @@ void sys_release(sie_op* op)
     op->kout.release(st);
     for (KrylovWork& k : op->kmulti) k.release(st);
     for (KrylovWork& k : op->kcs_multi) k.release(st);
+    op->kzp.release(st);
+    if (op->zp) cudaFreeAsync(op->zp, st);
+    op->zp = nullptr;
     for (void* p : {(void*)op->mscr, (void*)op->ir_multi, (void*)op->mvec})
         if (p) cudaFreeAsync(p, st);
     op->mscr = op->ir_multi = op->mvec = nullptr;
@@ -2108,6 +2187,256 @@ sie_status sys_far_sums(sie_op* op, const double2* x, const double* rhat_d, int 
     return SIE_OK;
 }
 
+// ------------------------------------------------------------------ panel Krylov solves
+// per right-hand side sizes inside a PanelWork
+static int64_t pw_p(int m) { return (int64_t)CGS_CHUNKS * (2 * (m + 1) + 1); }
+static int64_t pw_h(int m) { return 2 * (int64_t)(m + 2); }
+static int64_t pw_d(int m) { return (int64_t)(m + 1) * m + 2 * m + 2 * (m + 1); }
+static int64_t pw_s(int m) { return 8 + m + 1; }
+
+sie_status PanelWork::alloc(cudaStream_t st, int64_t n_, int m_, int R_)
+{
+    if (n_ == n && m_ == m && R_ == R) return SIE_OK;
+    release(st);
+    n = n_;
+    m = m_;
+    R = R_;
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&V, sizeof(double2) * (m + 1) * R * n, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&Z, sizeof(double2) * m * R * n, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&W, sizeof(double2) * R * n, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&Rv, sizeof(double2) * R * n, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&P, sizeof(double2) * R * pw_p(m), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&h, sizeof(double2) * R * pw_h(m), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&Hd, sizeof(double2) * R * pw_d(m), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&part, sizeof(double2) * R * DOT_CHUNKS, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&wd, sizeof(double2) * R, st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&sc, sizeof(double) * R * pw_s(m), st));
+    SIE_CUDA_TRY(cudaMallocAsync((void**)&res, sizeof(double) * R * (m + 1), st));
+    SIE_CUDA_TRY(cudaMallocHost((void**)&res_h, sizeof(double) * R * (m + 1)));
+    ev.resize(m + 1);
+    for (auto& e : ev) SIE_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return SIE_OK;
+}
+
+void PanelWork::release(cudaStream_t st)
+{
+    for (double2* p : {V, Z, W, Rv, P, h, Hd, part, wd})
+        if (p) cudaFreeAsync(p, st);
+    for (double* p : {sc, res})
+        if (p) cudaFreeAsync(p, st);
+    if (res_h) {
+        cudaStreamSynchronize(st);
+        cudaFreeHost(res_h);
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    ev.clear();
+    V = Z = W = Rv = P = h = Hd = part = wd = nullptr;
+    sc = res = res_h = nullptr;
+    n = 0;
+    m = R = 0;
+}
+
+// Restarted flexible GMRES for R right-hand sides held as panels (B, X: R
+// contiguous vectors of n), zero initial guess: the arithmetic of fgmres per
+// right-hand side, with A and Minv applied to a whole panel and every
+// Gram-Schmidt / Givens step one launch for all R (PanelStrides).  Ends when
+// every residual is below tol (host check lagged by one iteration); iters,
+// relres[q] as for fgmres.
+static sie_status fgmres_panel(sie_ctx* c, PanelWork& K, int R, int64_t n, const Apply& A, const Apply& Minv,
+                               const double2* B, double2* X, double tol, int maxit, int restart, int* iters_out,
+                               double* relres_out)
+{
+    cudaStream_t st = c->stream;
+    const int m = restart;
+    SIE_TRY(K.alloc(st, n, m, R));
+    PanelStrides ps;
+    ps.v = n;
+    ps.p = pw_p(m);
+    ps.h = pw_h(m);
+    ps.d = pw_d(m);
+    ps.s = pw_s(m);
+    const int64_t ldv = (int64_t)R * n;
+    auto Hq = [&](int q) { return K.Hd + q * ps.d; };
+    auto gq = [&](int q) { return K.Hd + q * ps.d + (m + 1) * m + 2 * m; };
+    auto yq = [&](int q) { return K.Hd + q * ps.d + (m + 1) * m + 2 * m + (m + 1); };
+    SIE_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double2) * R * n, st));
+    for (int q = 0; q < R; q++) {
+        SIE_TRY(dots(st, n, 1, B + q * n, n, B + q * n, K.part + q * DOT_CHUNKS, K.wd + q));
+        k_gm_start<<<nb(n), 256, 0, st>>>(n, B + q * n, K.wd + q, K.V + q * n, gq(q), m, K.sc + q * ps.s, 1);
+    }
+    SIE_CUDA_TRY(cudaGetLastError());
+    std::vector<double> rel(R, 1.0);
+    auto all_below = [&](const double* v) {
+        for (int q = 0; q < R; q++)
+            if (!(v[q] < tol)) return false;
+        return true;
+    };
+    int it = 0;
+    const int LAG = 1;
+    const dim3 grid(CGS_CHUNKS, R);
+    while (true) {
+        int j = 0;
+        bool conv = false;
+        for (; j < m && it < maxit; j++) {
+            double2* Vj = K.V + j * ldv;
+            double2* Zj = K.Z + j * ldv;
+            SIE_TRY(Minv(Vj, Zj));
+            SIE_TRY(A(Zj, K.W));
+            double2* P1 = K.P;
+            double2* P2 = K.P + (int64_t)CGS_CHUNKS * (m + 1);
+            double2* P3 = K.P + (int64_t)2 * CGS_CHUNKS * (m + 1);
+            k_cgs_part<<<grid, 256, 0, st>>>(n, j + 1, K.V, ldv, K.W, P1, m + 1, nullptr, nullptr, nullptr, ps);
+            k_cgs_update<<<grid, 256, 0, st>>>(n, j + 1, K.V, ldv, P1, m + 1, K.h, K.W, P2, 0, nullptr, ps);
+            k_cgs_update<<<grid, 256, 0, st>>>(n, j + 1, K.V, ldv, P2, m + 1, K.h + (m + 2), K.W, P3, 1, nullptr,
+                                               ps);
+            k_cgs_finish<<<grid, 256, 0, st>>>(n, j, m, K.h, K.h + (m + 2), P3, K.W, K.V, K.Hd,
+                                               K.Hd + (m + 1) * m, K.Hd + (m + 1) * m + m,
+                                               K.Hd + (m + 1) * m + 2 * m, K.sc, nullptr, ps, ldv, K.res);
+            SIE_CUDA_TRY(cudaGetLastError());
+            SIE_CUDA_TRY(cudaMemcpyAsync(K.res_h + (int64_t)j * R, K.res + (int64_t)j * R, sizeof(double) * R,
+                                         cudaMemcpyDeviceToHost, st));
+            SIE_CUDA_TRY(cudaEventRecord(K.ev[j], st));
+            it++;
+            if (j >= LAG) {
+                SIE_CUDA_TRY(cudaEventSynchronize(K.ev[j - LAG]));
+                const double* v = K.res_h + (int64_t)(j - LAG) * R;
+                for (int q = 0; q < R; q++)
+                    if (!std::isfinite(v[q])) {
+                        set_error("GMRES: the residual is not finite (non-finite right-hand side or operator)");
+                        return SIE_ERR_ARG;
+                    }
+                if (all_below(v)) {
+                    conv = true;
+                    j++;
+                    break;
+                }
+            }
+        }
+        const int jend = j - 1;
+        SIE_CUDA_TRY(cudaEventSynchronize(K.ev[jend]));
+        for (int q = 0; q < R; q++) {
+            rel[q] = K.res_h[(int64_t)jend * R + q];
+            if (!std::isfinite(rel[q])) {
+                set_error("GMRES: the residual is not finite (non-finite right-hand side or operator)");
+                return SIE_ERR_ARG;
+            }
+            k_gm_backsub<<<1, 1, 0, st>>>(jend, m, Hq(q), gq(q), yq(q));
+            k_gemv<<<nb(n), 256, 0, st>>>(n, jend + 1, K.Z + q * n, ldv, yq(q), 1.0, X + q * n);
+        }
+        SIE_CUDA_TRY(cudaGetLastError());
+        if (all_below(rel.data())) conv = true;
+        if (conv || it >= maxit) break;
+        // restart from the true residuals
+        SIE_TRY(A(X, K.W));
+        SIE_CUDA_TRY(cudaMemcpyAsync(K.Rv, B, sizeof(double2) * R * n, cudaMemcpyDeviceToDevice, st));
+        SIE_TRY(axpby(st, R * n, -1.0, K.W, 1.0, K.Rv));
+        std::vector<double> hb(2 * R);
+        for (int q = 0; q < R; q++) {
+            SIE_TRY(dots(st, n, 1, K.Rv + q * n, n, K.Rv + q * n, K.part + q * DOT_CHUNKS, K.wd + q));
+            k_gm_start<<<nb(n), 256, 0, st>>>(n, K.Rv + q * n, K.wd + q, K.V + q * n, gq(q), m, K.sc + q * ps.s, 0);
+            SIE_CUDA_TRY(cudaMemcpyAsync(K.res_h + 2 * q, K.sc + q * ps.s, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                         st));
+        }
+        SIE_CUDA_TRY(cudaGetLastError());
+        SIE_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int q = 0; q < R; q++) rel[q] = K.res_h[2 * q] > 0 ? K.res_h[2 * q + 1] / K.res_h[2 * q] : 0.0;
+        if (all_below(rel.data())) break;
+    }
+    for (int q = 0; q < R; q++) {
+        if (iters_out) iters_out[q] = it;
+        if (relres_out) relres_out[q] = rel[q];
+    }
+    return all_below(rel.data()) ? SIE_OK : SIE_ERR_NOT_CONVERGED;
+}
+
+// E = Z' H for a panel of R vectors (near-region-only or SIBC interiors): the
+// right-hand sides of the nested solves by CSR x panel products, then one
+// panel FGMRES for all R (near-only: A = L_i,NR, M = its sparse approximate
+// inverse; SIBC: A = Gram, M = Jacobi), with the stream path's iteration cap
+// and tolerance; then the impedance factor.  Hp, Ep: R x ne.
+static sie_status apply_Z_panel(sie_op* op, int R, const double2* Hp, double2* Ep, double* nested_res)
+{
+    sie_ctx* c = op->mesh->ctx;
+    cudaStream_t st = c->stream;
+    const int64_t ne = op->mesh->h.ne;
+    AimOp& I = op->inn;
+    const bool sibc = op->p.interior_model == SIE_SIBC;
+    double2* a = op->zp + 2 * MULTI_RHS * ne;  // right-hand sides
+    double2* t = op->zp + 3 * MULTI_RHS * ne;  // scratch
+    // I-cross H (weight -1/2 for GIBC, +1 for SIBC)
+    SIE_TRY(csr_panel(st, (int)ne, op->ix_row_ptr, op->ix_col, op->ix_val, Hp, ne, R, false, t, ne));
+    if (sibc) {
+        SIE_CUDA_TRY(cudaMemcpyAsync(a, t, sizeof(double2) * R * ne, cudaMemcpyDeviceToDevice, st));
+    } else {
+        SIE_TRY(csr_panel(st, (int)ne, I.row_ptr, I.col, I.valK, Hp, ne, R, false, a, ne));
+        SIE_TRY(axpby(st, R * ne, -0.5, t, 1.0, a));
+    }
+    auto A = [&](const double2* x, double2* y) {
+        if (sibc) return csr_panel(st, (int)ne, op->gr_row_ptr, op->gr_col, op->gr_val, x, ne, R, false, y, ne);
+        return csr_panel(st, (int)ne, I.row_ptr, I.col, I.valL, x, ne, R, false, y, ne);
+    };
+    auto M = [&](const double2* x, double2* y) {
+        if (sibc) {
+            for (int q = 0; q < R; q++)
+                k_jacobi<<<nb(ne), 256, 0, st>>>(ne, x + q * ne, op->gr_diag, make_double2(1.0, 0.0), y + q * ne);
+            SIE_CUDA_TRY(cudaGetLastError());
+            return SIE_OK;
+        }
+        return csr_panel(st, (int)ne, I.row_ptr, I.col, I.valM, x, ne, R, false, y, ne);
+    };
+    const int m_in = inner_m(op);
+    int it[MULTI_RHS];
+    double rr[MULTI_RHS];
+    sie_status s;
+    {
+        Stage s_(c, "inner_solve");
+        s = fgmres_panel(c, op->kzp, R, ne, A, M, a, Ep, op->p.tol_inner, m_in, m_in, it, rr);
+    }
+    if (s != SIE_OK && s != SIE_ERR_NOT_CONVERGED) return s;
+    double worst = 0;
+    for (int q = 0; q < R; q++) {
+        worst = std::max(worst, rr[q]);
+        op->stats[2] = std::max(op->stats[2], (double)it[q]);
+        op->stats[3] = std::max(op->stats[3], rr[q]);
+    }
+    if (nested_res) *nested_res = worst;
+    if (op->edge_zf) {
+        for (int q = 0; q < R; q++) k_scale_edges<<<nb(ne), 256, 0, st>>>(ne, op->edge_zf, Ep + q * ne);
+        SIE_CUDA_TRY(cudaGetLastError());
+        return SIE_OK;
+    }
+    cplx f;
+    if (sibc) {
+        f = cplx(op->eta_re, op->eta_im);
+    } else {
+        cplx zs(0.0, op->k0 * op->eps_r);
+        zs += op->sigma * ETA0;
+        f = -1.0 / zs;
+    }
+    return axpby(st, R * ne, f, Ep, 0.0, Ep);
+}
+
+// y_q = SYS x_q for R vectors (block product): the R nested interior solves as
+// one panel solve (near-region-only and SIBC interiors; AIM interiors solve
+// each through apply_Z), then the rest of the product per vector.
+static sie_status apply_sys_multi(sie_op* op, int R, const double2* const* x, double2* const* y)
+{
+    if (op->inn.has_grid && op->p.interior_model != SIE_SIBC) {
+        for (int q = 0; q < R; q++) SIE_TRY(apply_sys(op, x[q], y[q]));
+        return SIE_OK;
+    }
+    cudaStream_t st = op->mesh->ctx->stream;
+    const int64_t ne = op->mesh->h.ne;
+    if (!op->zp) SIE_CUDA_TRY(cudaMallocAsync((void**)&op->zp, sizeof(double2) * 4 * MULTI_RHS * ne, st));
+    double2* Hp = op->zp;
+    double2* Ep = op->zp + MULTI_RHS * ne;
+    for (int q = 0; q < R; q++)
+        SIE_CUDA_TRY(cudaMemcpyAsync(Hp + q * ne, x[q], sizeof(double2) * ne, cudaMemcpyDeviceToDevice, st));
+    SIE_TRY(apply_Z_panel(op, R, Hp, Ep, nullptr));
+    for (int q = 0; q < R; q++) SIE_TRY(apply_sys_rest(op, x[q], Ep + q * ne, x[q] + ne, y[q]));
+    return SIE_OK;
+}
+
 // ------------------------------------------------------------------ several right-hand sides in lockstep
 // y_q = Op x_q for q < R: a non-owning reference to a block operator
 class BlockApply {
@@ -2376,11 +2705,19 @@ sie_status sys_solve_multi(sie_op* op, int R, const double2* const* b, double2* 
         tw[q] = op->mscr + q * multi_stride(op);
         bw[q] = tw[q] + n;
     }
+    // the block product (panel nested solves), or one product per vector
+    // (graph replays) with SIE_BLOCK_PRODUCT=0 in the environment
+    static const bool block = [] {
+        const char* e = getenv("SIE_BLOCK_PRODUCT");
+        return !(e && e[0] == '0');
+    }();
     auto A = [&](int Rn, const double2* const* u, double2* const* v) {
-        for (int q = 0; q < Rn; q++) {
-            SIE_TRY(apply_sys_fast(op, u[q], v[q]));
-            SIE_TRY(weight_rows(op, v[q], v[q], false));
+        if (block && Rn > 1) {
+            SIE_TRY(apply_sys_multi(op, Rn, u, v));
+        } else {
+            for (int q = 0; q < Rn; q++) SIE_TRY(apply_sys_fast(op, u[q], v[q]));
         }
+        for (int q = 0; q < Rn; q++) SIE_TRY(weight_rows(op, v[q], v[q], false));
         return SIE_OK;
     };
     auto Minv = [&](int Rn, const double2* const* u, double2* const* v) {

@@ -1,6 +1,7 @@
 """Several right-hand sides solved in lockstep (sie_solve with nrhs > 1): one
 Krylov basis per right-hand side, the system product and the constraint
-preconditioner applied to the block's vectors together.  Each solution must
+preconditioner applied to the block's vectors together (near-region-only and
+SIBC interiors: the block's nested interior solves as one panel solve).  Each solution must
 be the one the right-hand side gets when solved alone (sequential path), to
 the solver tolerance amplified by the conditioning, every residual must be
 below tol_outer, and the backscatter RCS within 1% of the Mie series; blocks
@@ -28,12 +29,13 @@ def _dirs(k, seed):
     return out
 
 
-@pytest.fixture(scope="module", params=[(1e-3, 10e9, 1.0, 5.8e7), (0.01, 3e9, 4.0, 0.0)], ids=["copper", "dielectric"])
+@pytest.fixture(scope="module", params=[(1e-3, 10e9, 1.0, 5.8e7, 0), (0.01, 3e9, 4.0, 0.0, 0),
+                                        (1e-3, 10e9, 1.0, 5.8e7, 1)], ids=["copper", "dielectric", "copper-sibc"])
 def case(request, lib, ctx):
-    radius, f, eps_r, sigma = request.param
+    radius, f, eps_r, sigma, model = request.param
     V, T = icosphere(2, radius, equal_volume=True)
     mesh = lib.Mesh(ctx, V, T)
-    op = lib.Operator(mesh, f, eps_r, 1.0, sigma, lib.params(tol_outer=1e-7, tol_inner=1e-10))
+    op = lib.Operator(mesh, f, eps_r, 1.0, sigma, lib.params(tol_outer=1e-7, tol_inner=1e-10, interior_model=model))
     dirs = _dirs(10, 31)
     B = np.stack([op.rhs_planewave(kh, ep) for kh, ep in dirs])
     ref = mie.backscatter_rcs(radius, f, eps_r, sigma)
