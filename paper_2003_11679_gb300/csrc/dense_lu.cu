@@ -475,57 +475,79 @@ __global__ void __launch_bounds__(256) k_cgemv_inv1(int n, const float2* __restr
 
 // X B for up to MULTI_R right-hand sides at once (the explicit inverse read
 // once for all of them): B packed as R complex64 vectors of n (n even).  A CTA
-// takes MR_ROWS rows (4 per warp) and walks the columns in chunks of
+// takes MR_ROWS rows (2 per warp) and walks the columns in chunks of
 // MR_CHUNK entry pairs; each chunk of B (R x MR_CHUNK float4) is staged in
 // shared memory and read by every warp, the matrix streams from HBM once.
-// FP32 products and per-lane sums, warp sums in FP64; out: pointers to the R
-// complex128 results.
+// Within a chunk a lane takes 4 column steps at a time (8 loads of 16 bytes
+// for its 2 rows), and the next 4 steps' loads are issued before the current
+// ones are used, so about 16 loads per lane stay in flight.  FP32 products
+// and per-lane sums, warp sums in FP64; out: pointers to the R complex128
+// results.
 constexpr int MULTI_R = 8;
-constexpr int MR_ROWS = 32;
-constexpr int MR_CHUNK = 128;
+constexpr int MR_WROWS = 2;
+constexpr int MR_ROWS = 8 * MR_WROWS;
+constexpr int MR_CHUNK = 512;
 struct OutPtrs {
     double2* p[MULTI_R];
 };
 __global__ void __launch_bounds__(256, 2) k_cgemm_inv_multi(int n, int R, const float4* __restrict__ X,
-                                                         const float4* __restrict__ B, OutPtrs out)
+                                                            const float4* __restrict__ B, OutPtrs out)
 {
-    __shared__ float4 Bs[MULTI_R][MR_CHUNK];
+    extern __shared__ float4 Bs[];  // [MULTI_R][MR_CHUNK]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = blockIdx.x * MR_ROWS + warp * 4;
+    const int r0 = blockIdx.x * MR_ROWS + warp * MR_WROWS;
     const int h = n / 2;
-    float ar[4][MULTI_R], ai[4][MULTI_R];
+    float ar[MR_WROWS][MULTI_R], ai[MR_WROWS][MULTI_R];
 #pragma unroll
-    for (int g = 0; g < 4; g++)
+    for (int g = 0; g < MR_WROWS; g++)
 #pragma unroll
         for (int q = 0; q < MULTI_R; q++) ar[g][q] = ai[g][q] = 0.f;
-    const float4* rows[4];
+    const float4* rows[MR_WROWS];
 #pragma unroll
-    for (int g = 0; g < 4; g++) rows[g] = X + (int64_t)min(r0 + g, n - 1) * h;
+    for (int g = 0; g < MR_WROWS; g++) rows[g] = X + (int64_t)min(r0 + g, n - 1) * h;
+    auto load = [&](float4 (&m)[4][MR_WROWS], int base, int cl, int c0) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int c = base + lane + 32 * u;
+#pragma unroll
+            for (int g = 0; g < MR_WROWS; g++)
+                m[u][g] = c < cl ? __ldg(rows[g] + c0 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
     for (int c0 = 0; c0 < h; c0 += MR_CHUNK) {
         const int cl = min(MR_CHUNK, h - c0);
         __syncthreads();
         for (int i = threadIdx.x; i < MULTI_R * MR_CHUNK; i += blockDim.x) {
             const int q = i / MR_CHUNK, c = i % MR_CHUNK;
-            Bs[q][c] = (q < R && c < cl) ? B[(int64_t)q * h + c0 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            Bs[q * MR_CHUNK + c] = (q < R && c < cl) ? B[(int64_t)q * h + c0 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        float4 cur[4][MR_WROWS], nxt[4][MR_WROWS];
+        load(cur, 0, cl, c0);
         __syncthreads();
-        for (int c = lane; c < cl; c += 32) {
-            float4 m[4];
+        for (int base = 0; base < MR_CHUNK; base += 128) {
+            if (base + 128 < MR_CHUNK) load(nxt, base + 128, cl, c0);
 #pragma unroll
-            for (int g = 0; g < 4; g++) m[g] = __ldg(rows[g] + c0 + c);
+            for (int u = 0; u < 4; u++) {
+                const int c = base + lane + 32 * u;
 #pragma unroll
-            for (int q = 0; q < MULTI_R; q++) {
-                const float4 v = Bs[q][c];
+                for (int q = 0; q < MULTI_R; q++) {
+                    const float4 v = Bs[q * MR_CHUNK + c];
 #pragma unroll
-                for (int g = 0; g < 4; g++) {
-                    ar[g][q] = fmaf(m[g].x, v.x, fmaf(-m[g].y, v.y, fmaf(m[g].z, v.z, fmaf(-m[g].w, v.w, ar[g][q]))));
-                    ai[g][q] = fmaf(m[g].x, v.y, fmaf(m[g].y, v.x, fmaf(m[g].z, v.w, fmaf(m[g].w, v.z, ai[g][q]))));
+                    for (int g = 0; g < MR_WROWS; g++) {
+                        const float4 mm = cur[u][g];
+                        ar[g][q] = fmaf(mm.x, v.x, fmaf(-mm.y, v.y, fmaf(mm.z, v.z, fmaf(-mm.w, v.w, ar[g][q]))));
+                        ai[g][q] = fmaf(mm.x, v.y, fmaf(mm.y, v.x, fmaf(mm.z, v.w, fmaf(mm.w, v.z, ai[g][q]))));
+                    }
                 }
             }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int g = 0; g < MR_WROWS; g++) cur[u][g] = nxt[u][g];
         }
     }
 #pragma unroll
-    for (int g = 0; g < 4; g++)
+    for (int g = 0; g < MR_WROWS; g++)
 #pragma unroll
         for (int q = 0; q < MULTI_R; q++) {
             double sr = ar[g][q], si = ai[g][q];
@@ -706,7 +728,11 @@ sie_status DenseLU::solve_multi(cudaStream_t st, int R, const double2* const* b,
         k_c128_to_c64<<<(n + 255) / 256, 256, 0, st>>>(n, b[q], bpack + (size_t)q * n);
         o.p[q] = x[q];
     }
-    k_cgemm_inv_multi<<<(unsigned)((n + MR_ROWS - 1) / MR_ROWS), 256, 0, st>>>(
+    const size_t smem = sizeof(float4) * MULTI_R * MR_CHUNK;  // 64 KB
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_cgemm_inv_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    SIE_CUDA_TRY(attr);
+    k_cgemm_inv_multi<<<(unsigned)((n + MR_ROWS - 1) / MR_ROWS), 256, smem, st>>>(
         n, R, reinterpret_cast<const float4*>(Xinv), reinterpret_cast<const float4*>(bpack), o);
     SIE_CUDA_TRY(cudaGetLastError());
     return SIE_OK;
