@@ -192,6 +192,11 @@ def stage_model(stage, info, ne, nt, nnz_ext, nnz_int):
         # Ix E (5 nnz/row), triangle Lphi product (info[7] pairs), vectors
         "spmv_sys": (nnz_ext * (2 * c + 4) + 5 * ne * (c + 4) + int(info[7]) * (c + 4) + 8 * ne * c + 6 * nt * c,
                      16.0 * nnz_ext + 8.0 * int(info[7])),
+        # k_spmv2 alone: both value arrays and the columns once, row pointers,
+        # H and E read once, y read and written
+        "spmv_near_ext": (nnz_ext * (2 * c + 4) + (ne + 1) * 8 + 4 * ne * c, 16.0 * nnz_ext),
+        # the rest of the product's sparse steps: I-cross E, triangle Lphi, vectors
+        "spmv_sys_rest": (5 * ne * (c + 4) + int(info[7]) * (c + 4) + 4 * ne * c + 6 * nt * c, 8.0 * int(info[7])),
     }
     r = table.get(stage)
     if r is not None and stage in FFT_GRIDS:
@@ -361,6 +366,16 @@ def run_ours(args):
                     "peak_note": f"HBM copy, {kind}"}
         roof.update({"algorithmic_bytes": B, "algorithmic_flops": F, "avg_launch_us": avg_s * 1e6,
                      "launches": dcount})
+    # every modelled stage of the FP64 path: fraction of the FP64 FMA and HBM peaks
+    stage_roofs = {}
+    for k, (tms, cnt) in kern.items():
+        mdl = stage_model(k, info, ne, nt, info[8], nnz_int)
+        if mdl is None or cnt == 0:
+            continue
+        a_s = tms * 1e-3 / cnt
+        stage_roofs[k] = {"avg_launch_us": round(a_s * 1e6, 2),
+                          "fp64_frac": round(mdl[1] / a_s / 1e12 / fp64_peak, 4),
+                          "hbm_frac": round(mdl[0] / a_s / 1e9 / peaks["hbm_gbs"], 4)}
     if graph_state & 1:
         # graph replay: nodes outside the nested loop + loop-body nodes per nested
         # iteration (upper bound: the largest iteration count of the timed loop)
@@ -395,6 +410,7 @@ def run_ours(args):
         "mixed_precision": mixed_line(ne, args, ms32, prof32, mixed_err, info, peaks, kind),
         "stages_ms": {k: round(v[0], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
         "roofline": roof,
+        "stage_rooflines": stage_roofs,
         "fma_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak, "how": "sie_probe_fma, this run"},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
@@ -419,7 +435,11 @@ def mixed_line(ne, args, ms32, prof, err, info, peaks, kind):
              "specmul_sys32": (7 + 4 + 4) * nx * ny * nz * c,
              "fft_z_specmul": (11 * nx * ny * Nz + 4 * nx * ny * nz) * c,
              # complex64 exterior near values (LA, K; triangle Lphi), FP64 I-cross and vectors
-             "spmv_sys": nnz_ext * (2 * c + 4) + ntri * (c + 4) + 5 * ne * 20 + 8 * ne * 16 + 6 * (n_t(info, ne)) * 16}
+             "spmv_sys": nnz_ext * (2 * c + 4) + ntri * (c + 4) + 5 * ne * 20 + 8 * ne * 16 + 6 * (n_t(info, ne)) * 16,
+             # k_spmv2_c64 alone: interleaved complex64 values and columns once,
+             # row pointers, the packed (H, E) read once, y (FP64) read and written
+             "spmv_near_ext": nnz_ext * (2 * c + 4) + (ne + 1) * 8 + ne * 2 * c + 2 * ne * 16,
+             "spmv_sys_rest": ntri * (c + 4) + 5 * ne * 20 + 4 * ne * 16 + 6 * (n_t(info, ne)) * 16}
     kern = {k: v for k, v in prof.items() if k in model}
     roof = None
     if kern:
@@ -427,9 +447,15 @@ def mixed_line(ne, args, ms32, prof, err, info, peaks, kind):
         B = model[dom] * FFT_GRIDS.get(dom, 1)
         avg = kern[dom][0] * 1e-3 / kern[dom][1]
         roof = {"bound": "hbm", "kernel": dom, "achieved": B / avg / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": B / avg / 1e9 / peaks["hbm_gbs"], "traffic": None, "peak_note": f"HBM copy, {kind}",
+                "frac": B / avg / 1e9 / peaks["hbm_gbs"], "traffic": traffic_of(dom, "mixed"),
+                "peak_note": f"HBM copy, {kind}",
                 "algorithmic_bytes": int(B), "avg_launch_us": avg * 1e6}
+    stage_roofs = {k: {"avg_launch_us": round(v[0] * 1e3 / v[1], 2),
+                       "hbm_frac": round(model[k] * FFT_GRIDS.get(k, 1) / (v[0] * 1e-3 / v[1]) / 1e9 /
+                                         peaks["hbm_gbs"], 4)}
+                   for k, v in kern.items() if v[1]}
     return {"value": ne * args.steps / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32 / args.steps,
+            "stage_rooflines": stage_roofs,
             "dtype": "c64 grid / f64 near+Krylov", "rel_err_vs_fp64": err,
             "stages_ms": {k: round(v[0], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
             "roofline": roof}

@@ -1451,19 +1451,22 @@ static sie_status apply_sys_rest(sie_op* op, const double2* H, const double2* E,
         }
     }
     {
-        Stage s_(c, "spmv_sys");
         const bool c64 = op->p.precision == SIE_MIXED && X.valLK32;
-        if (c64) {
-            k_pack_he32<<<nb(ne), 256, 0, st>>>((int)ne, H, E, op->pk_he);
-            k_spmv2_c64<<<(unsigned)((ne + 3) / 4), 128, 0, st>>>((int)ne, X.row_ptr, X.col, X.valLK32, op->pk_he,
-                                                                   make_double2(0.0, op->k0),
+        if (c64) k_pack_he32<<<nb(ne), 256, 0, st>>>((int)ne, H, E, op->pk_he);
+        {
+            // the exterior near-region product alone (one kernel)
+            Stage s1_(c, "spmv_near_ext");
+            if (c64)
+                k_spmv2_c64<<<(unsigned)((ne + 3) / 4), 128, 0, st>>>((int)ne, X.row_ptr, X.col, X.valLK32,
+                                                                       op->pk_he, make_double2(0.0, op->k0),
+                                                                       make_double2(-1.0, 0.0), y1);
+            else
+                k_spmv2<<<(unsigned)((ne + 3) / 4), 128, 0, st>>>((int)ne, X.row_ptr, X.col, X.valLA, H,
+                                                                   make_double2(0.0, op->k0), X.valK, E,
                                                                    make_double2(-1.0, 0.0), y1);
-        } else {
-            k_spmv2<<<(unsigned)((ne + 3) / 4), 128, 0, st>>>((int)ne, X.row_ptr, X.col, X.valLA, H,
-                                                               make_double2(0.0, op->k0), X.valK, E,
-                                                               make_double2(-1.0, 0.0), y1);
+            SIE_CUDA_TRY(cudaGetLastError());
         }
-        SIE_CUDA_TRY(cudaGetLastError());
+        Stage s_(c, "spmv_sys_rest");
         SIE_TRY(spmv(st, (int)ne, op->ix_nnz, op->ix_row_ptr, op->ix_col, op->ix_val, E, cplx(-0.5, 0.0), y1));
         double2* phi = op->sys_tmp + nt;
         if (c64) {
