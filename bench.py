@@ -16,6 +16,10 @@ dielectric-sphere workload (1,920 RWG, equal-volume mesh), FP64 and with
 mixed-precision iterative refinement on the same right-hand sides, each solve's
 backscatter RCS checked against the Mie series (1%).
 
+A ports leg drives a copper bar through two delta-gap ports (sie_port_*) and
+reports its admittance and S parameters at a few frequencies, with the
+near-region-only interior and with the surface impedance comparator.
+
 The FP64 path's roofline fractions use the FP64 FMA throughput the library's
 probe kernel measures in the same run (sie_probe_fma).
 
@@ -333,6 +337,12 @@ def run_ours(args):
             batching = batching_stats(sie, ctx, args)
         except Exception as e:  # reported, not fatal to the line
             batching = {"error": f"{type(e).__name__}: {e}"[:300]}
+    ports = None
+    if not args.no_solve and args.port_freqs and rank == 0:
+        try:
+            ports = ports_stats(sie, ctx, args)
+        except Exception as e:  # reported, not fatal to the line
+            ports = {"error": f"{type(e).__name__}: {e}"[:300]}
     serving = None
     if not args.no_solve and args.serve_requests > 0 and rank == 0:
         try:
@@ -405,6 +415,7 @@ def run_ours(args):
         "solves": solves,
         "solves_workload": lossy_solves,
         "batching": batching,
+        "ports": ports,
         "serving": serving,
         "block_rhs": block,
         "mixed_precision": mixed_line(ne, args, ms32, prof32, mixed_err, info, peaks, kind),
@@ -677,6 +688,43 @@ def batching_stats(sie, ctx, args):
     return out
 
 
+def ports_stats(sie, ctx, args):
+    """Ports (the delta-gap model of sie_port_*): a copper bar, 40 x 4 x 4 um
+    (structured mesh of 336 triangles / 504 RWG), with two ports across its
+    cross-section at x = -10 um and +10 um; the admittance matrix (both
+    ports in one lockstep solve block, tolerance 1e-4 as in Sec. V) and S
+    (50 ohm) at each frequency of args.port_freqs, with the near-region-only
+    interior and with the surface impedance comparator.  Reports the time
+    per admittance matrix and the reciprocity |Y12 - Y21| / |Y12|."""
+    from synth import box
+    V, T = box((40e-6, 4e-6, 4e-6), (20, 2, 2))
+    pts = [((-10e-6, 0.0, 0.0), (1.0, 0.0, 0.0), 8e-6), ((10e-6, 0.0, 0.0), (1.0, 0.0, 0.0), 8e-6)]
+    mesh = sie.Mesh(ctx, V, T)
+    rows, t_tot, n_y = [], 0.0, 0
+    try:
+        for model, name in ((sie.SIE_GIBC, "gibc"), (sie.SIE_SIBC, "sibc")):
+            for f in args.port_freqs:
+                op = sie.Operator(mesh, f * 1e9, 1.0, 1.0, 5.8e7, sie.params(interior_model=model))
+                try:
+                    op.port_admittance(pts, check=False)  # workspaces and graph, untimed
+                    t0 = time.perf_counter()
+                    Y, it, rr = op.port_admittance(pts, check=False)
+                    t_tot += time.perf_counter() - t0
+                    n_y += 1
+                    S = sie.port_sparams(Y, 50.0)
+                    rows.append({"interior": name, "f_ghz": f, "near_only": bool(op.info()[9] == 1.0),
+                                 "Y11": [Y[0, 0].real, Y[0, 0].imag], "Y21": [Y[1, 0].real, Y[1, 0].imag],
+                                 "S11": [S[0, 0].real, S[0, 0].imag], "S21": [S[1, 0].real, S[1, 0].imag],
+                                 "reciprocity": float(abs(Y[0, 1] - Y[1, 0]) / abs(Y[0, 1])),
+                                 "iters": it.tolist(), "relres": rr.tolist()})
+                finally:
+                    op.close()
+    finally:
+        mesh.close()
+    return {"workload": "copper bar 40x4x4 um, 336 triangles, 2 ports", "rows": rows,
+            "ms_per_admittance": 1e3 * t_tot / max(n_y, 1)}
+
+
 def serve_catalogue():
     """The serving trace's operators: (name, radius, f, eps_r, sigma, level,
     Mie backscatter) as drawn and evaluated by tests/golden/make_mie_backscatter.py."""
@@ -868,6 +916,8 @@ def main():
     ap.add_argument("--lossy-solves", type=int, default=3)
     ap.add_argument("--lockstep-rhs", type=int, default=8)
     ap.add_argument("--batch-rhs", type=int, default=16)
+    ap.add_argument("--port-freqs", type=float, nargs="*", default=[20.0, 50.0, 100.0],
+                    help="frequencies (GHz) of the ports leg; none to skip it")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--interior", default="gibc", choices=["gibc", "sibc"],

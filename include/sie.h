@@ -350,6 +350,70 @@ sie_status sie_rcs(sie_op* op, const double* x, const double* rhat, int ndir, do
  * direction, far-field sum and cross section that it reads back. */
 sie_status sie_rcs_static(sie_op* op, const double* x, const double* rhat, int ndir, double* rcs, int flags);
 
+/* Ports (delta gap).  Sec. II admits a port excitation in place of the plane
+ * wave, and Sec. V extracts the S parameters of its copper package and
+ * interconnect examples through ports, but the paper only cites the port
+ * model.  The library's model is the delta gap:
+ *   - a port is a closed loop of mesh edges cutting a conductor's surface:
+ *     the edges whose two end points lie in the plane through `origin` with
+ *     normal `normal` (within 1e-6 mean edge lengths) and within `radius`
+ *     of `origin`.  Each of them must have its two triangles on opposite
+ *     sides of the plane, and the mesh must have vertices on the plane (a
+ *     structured mesh cut along one of its grid planes, for instance);
+ *   - `normal` is the port's reference direction: s_m = +1 when T+ of edge
+ *     m lies on the -normal side, else -1, and p_m = s_m l_m;
+ *   - a voltage V across port j is the impressed field V delta(xi) normal,
+ *     xi = normal . (r - origin), entering Eq. (EFIE01dis) as the incident
+ *     field does: b_m = -(V / eta0) p_m (charge rows zero);
+ *   - the current through the port along +normal is I = -p . H (the first
+ *     block of the solution holds the RWG coefficients of -n x H), so that
+ *     (1/2) Re(V I*) is the power the port delivers;
+ *   - Y_ij = I_i / V_j with every other port shorted (no impressed field),
+ *     S = (1 - z_ref Y)(1 + z_ref Y)^-1. */
+typedef struct {
+    double origin[3];   /* a point of the port plane (m)                         */
+    double normal[3];   /* plane normal = reference direction (any length > 0)   */
+    double radius;      /* only edges within this distance of origin (m)         */
+} sie_port;
+
+/* The edges of one port (ascending edge numbers) and their signs s_m.  Call
+ * with edge or sign NULL to get the count in *n; then with buffers of *n
+ * entries (host).  SIE_ERR_ARG when no edge qualifies, an edge in the plane
+ * does not separate its triangles, or the port's numbers are not finite. */
+sie_status sie_port_edges(const sie_mesh* mesh, const sie_port* port, int32_t* edge, int32_t* sign, int64_t* n);
+
+/* Right-hand sides of the ports: nport vectors of N_e + N_t complex128
+ * ([first block; zero charge rows], the layout of sie_solve), vector j with
+ * port j driven by volts[j] volts (volts NULL: 1 V) and the other ports
+ * shorted.  flags: SIE_DEVICE_PTRS for a device b.  Allocates and frees
+ * small device buffers; synchronises. */
+sie_status sie_rhs_ports(sie_op* op, const sie_port* ports, int nport, const double* volts, double* b, int flags);
+
+/* Port currents I = -p_i . H_r of nrhs solutions x (N_e + N_t complex128
+ * each, as sie_solve returns them): I[r * nport + i] (complex128, host).
+ * flags: SIE_DEVICE_PTRS for a device x.  Allocates and frees small device
+ * buffers; synchronises. */
+sie_status sie_port_currents(sie_op* op, const sie_port* ports, int nport, const double* x, int nrhs, double* I,
+                             int flags);
+
+/* Admittance matrix of the ports: one solve per port (sie_solve with nport
+ * right-hand sides, lockstep blocks of 8), then the port currents.
+ * Y: nport x nport complex128 row-major on the host, Y[i * nport + j] =
+ * current through port i per volt on port j.  iters, relres: per port (host
+ * arrays of nport, may be NULL).  flags: SIE_SOLVE_REFINE and
+ * SIE_SOLVE_SEQUENTIAL as in sie_solve (SIE_DEVICE_PTRS is refused: Y is a
+ * host array).  Returns SIE_ERR_NOT_CONVERGED, with Y from the last iterates,
+ * when a solve stopped at maxit or a nested solve ended above tol_inner. */
+sie_status sie_port_admittance(sie_op* op, const sie_port* ports, int nport, double* Y, int* iters, double* relres,
+                               int flags);
+
+/* S parameters from an admittance matrix for one real reference impedance
+ * z_ref (ohm) on every port: S = (1 - z_ref Y)(1 + z_ref Y)^-1.  Y, S:
+ * nport x nport complex128 row-major, host.  Host arithmetic only (Gaussian
+ * elimination with partial pivoting).  SIE_ERR_ARG when 1 + z_ref Y is
+ * singular or z_ref is not positive. */
+sie_status sie_port_sparams(int nport, const double* Y, double z_ref, double* S);
+
 /* x_q = A^-1 b_q for one dense complex matrix and nrhs right-hand sides with
  * the library's GPU LU, the one the constraint preconditioners use
  * (Sec. III-D: the paper factorises its preconditioner by LU): complex64

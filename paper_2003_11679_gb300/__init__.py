@@ -36,7 +36,8 @@ SYMBOLS = ["sie_params_default", "sie_ctx_create", "sie_ctx_destroy", "sie_last_
            "sie_mesh_destroy", "sie_mesh_counts", "sie_op_build", "sie_op_destroy", "sie_op_set_solver",
            "sie_op_stats", "sie_op_info", "sie_op_grid",
            "sie_matvec", "sie_op_near_csr", "sie_rhs_planewave", "sie_solve", "sie_rcs", "sie_rcs_static",
-           "sie_probe_fma", "sie_dense_solve", "sie_mesh_create_objects", "sie_set_material"]
+           "sie_probe_fma", "sie_dense_solve", "sie_mesh_create_objects", "sie_set_material",
+           "sie_port_edges", "sie_rhs_ports", "sie_port_currents", "sie_port_admittance", "sie_port_sparams"]
 
 
 class sie_params(ctypes.Structure):
@@ -52,6 +53,20 @@ class sie_params(ctypes.Structure):
                 ("q_ratio", ctypes.c_double), ("q_cf", ctypes.c_double), ("q_kres", ctypes.c_double),
                 ("q_alen", ctypes.c_double), ("q_oratio", ctypes.c_double), ("dense_pc_max", ctypes.c_int),
                 ("interior_model", ctypes.c_int)]
+
+
+class sie_port(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("normal", ctypes.c_double * 3), ("radius", ctypes.c_double)]
+
+
+def _ports(ports):
+    """ctypes array of sie_port from (origin, normal, radius) tuples."""
+    arr = (sie_port * len(ports))()
+    for a, (o, n, r) in zip(arr, ports):
+        a.origin[:] = [float(v) for v in o]
+        a.normal[:] = [float(v) for v in n]
+        a.radius = float(r)
+    return arr
 
 
 class SieError(RuntimeError):
@@ -95,6 +110,11 @@ def lib():
         L.sie_dense_solve.argtypes = [I, I, I, P, P, P, I]
         L.sie_mesh_create_objects.argtypes = [P, P, I64, P, I64, P, PP, P]
         L.sie_set_material.argtypes = [P, I, D, D, D]
+        L.sie_port_edges.argtypes = [P, P, P, P, P]
+        L.sie_rhs_ports.argtypes = [P, P, I, P, P, I]
+        L.sie_port_currents.argtypes = [P, P, I, P, I, P, I]
+        L.sie_port_admittance.argtypes = [P, P, I, P, P, P, I]
+        L.sie_port_sparams.argtypes = [I, P, D, P]
         for name in SYMBOLS:
             f = getattr(L, name)
             if name not in ("sie_params_default", "sie_last_error"):
@@ -127,6 +147,14 @@ def dense_solve(A, b, device=0, inverse=False):
     nrhs = 1 if b.ndim == 1 else b.shape[0]
     _check(lib().sie_dense_solve(device, n, nrhs, A.ctypes.data, b.ctypes.data, x.ctypes.data, 1 if inverse else 0))
     return x
+
+
+def port_sparams(Y, z_ref=50.0):
+    """S = (1 - z_ref Y)(1 + z_ref Y)^-1 (the library's host routine)."""
+    Y = np.ascontiguousarray(np.atleast_2d(Y), dtype=np.complex128)
+    S = np.zeros_like(Y)
+    _check(lib().sie_port_sparams(len(Y), Y.ctypes.data, float(z_ref), S.ctypes.data))
+    return S
 
 
 def params(**kw):
@@ -208,6 +236,16 @@ class Mesh:
         c = np.zeros(3, np.int64)
         _check(lib().sie_mesh_counts(self.h, c.ctypes.data))
         self.ne, self.nt, self.nv = int(c[0]), int(c[1]), int(c[2])
+
+    def port_edges(self, port):
+        """(edges, signs) of one port (origin, normal, radius)."""
+        n = ctypes.c_int64()
+        pt = _ports([port])
+        _check(lib().sie_port_edges(self.h, pt, None, None, ctypes.byref(n)))
+        e = np.zeros(n.value, np.int32)
+        s = np.zeros(n.value, np.int32)
+        _check(lib().sie_port_edges(self.h, pt, e.ctypes.data, s.ctypes.data, ctypes.byref(n)))
+        return e, s
 
     def set_material(self, obj, eps_r, mu_r=1.0, sigma=0.0):
         _check(lib().sie_set_material(self.h, obj, eps_r, mu_r, sigma))
@@ -318,6 +356,39 @@ class Operator:
         _check(lib().sie_rcs_static(self.h, px, rh.ctypes.data, len(rh), out.ctypes.data,
                                     SIE_DEVICE_PTRS if dx else 0))
         return out
+
+    def rhs_ports(self, ports, volts=None, out=None):
+        """One right-hand side per port (N_e + N_t each), port j driven with
+        volts[j] (1 V by default), the others shorted.  ports: (origin,
+        normal, radius) tuples."""
+        n = self.mesh.ne + self.mesh.nt
+        b = out if out is not None else np.zeros((len(ports), n), np.complex128)
+        v = None if volts is None else np.ascontiguousarray(volts, dtype=np.float64)
+        pb, dev = _ptr(b)
+        _check(lib().sie_rhs_ports(self.h, _ports(ports), len(ports), None if v is None else v.ctypes.data, pb,
+                                   SIE_DEVICE_PTRS if dev else 0))
+        return b
+
+    def port_currents(self, ports, x, nrhs=1):
+        """I[r, i]: current through port i of solution r."""
+        I = np.zeros((nrhs, len(ports)), np.complex128)
+        px, dev = _ptr(x)
+        _check(lib().sie_port_currents(self.h, _ports(ports), len(ports), px, nrhs, I.ctypes.data,
+                                       SIE_DEVICE_PTRS if dev else 0))
+        return I
+
+    def port_admittance(self, ports, refine=False, sequential=False, check=True):
+        """(Y, iters, relres): Y[i, j] = current through port i per volt on port j."""
+        n = len(ports)
+        Y = np.zeros((n, n), np.complex128)
+        it = np.zeros(n, np.int32)
+        rr = np.zeros(n)
+        flags = (SIE_SOLVE_REFINE if refine else 0) | (SIE_SOLVE_SEQUENTIAL if sequential else 0)
+        code = lib().sie_port_admittance(self.h, _ports(ports), n, Y.ctypes.data, it.ctypes.data, rr.ctypes.data,
+                                         flags)
+        if check or code != SIE_ERR_NOT_CONVERGED:
+            _check(code)
+        return Y, it, rr
 
     def close(self):
         if self.h:
