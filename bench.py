@@ -916,7 +916,7 @@ def main():
     ap.add_argument("--lossy-solves", type=int, default=3)
     ap.add_argument("--lockstep-rhs", type=int, default=8)
     ap.add_argument("--batch-rhs", type=int, default=16)
-    ap.add_argument("--port-freqs", type=float, nargs="*", default=[20.0, 50.0, 100.0],
+    ap.add_argument("--port-freqs", type=float, nargs="*", default=[50.0, 100.0, 200.0],
                     help="frequencies (GHz) of the ports leg; none to skip it")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=50.0)

@@ -1,9 +1,14 @@
 """sie_rcs_static, the allocation-free variant of sie_rcs, through the C ABI.
 
-Both entry points run the same nested interior solve and far-field kernel, so
-the cross sections agree up to the rounding of the last step (host vs device
-evaluation of |N_perp(H) + rhat x N(E')|^2): tolerance 1e-12 of the largest
-value.  Two calls in a row with different direction sets check that nothing
+Both entry points run the same nested interior solve and far-field kernel.
+With the near-region-only interior every product of that solve is
+reproducible to the bit, so the cross sections agree up to the rounding of
+the last step (host vs device evaluation of |N_perp(H) + rhat x N(E')|^2):
+1e-12 of the largest value.  With the interior on the AIM grid (the
+dielectric sphere) the interior L and K products project with FP64 atomic
+additions, whose order varies from call to call; each call's nested solve
+(tol_inner 1e-6) then ends on an iterate that differs at the rounding level
+amplified by the solve (2e-11 of the largest value measured): 1e-9.  Two calls in a row with different direction sets check that nothing
 left in the shared device array leaks into the next call.  The file is
 collected last so that it also runs after every other GPU test.
 """
@@ -16,7 +21,7 @@ from synth import icosphere
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-12
+TOL = {"dielectric": 1e-9, "lossy": 1e-12}
 
 
 def _dirs(n, seed):
@@ -52,6 +57,7 @@ def solved(request, lib, ctx):
         s = Solved(lib, ctx, 2, 0.01, 3e9, 4.0, 0.0)
     else:
         s = Solved(lib, ctx, 2, 1e-3, 10e9, 1.0, 1e4)
+    s.tol = TOL[request.param]
     yield s
     s.op.close()
     s.gm.close()
@@ -70,11 +76,11 @@ def test_two_calls_in_a_row_match_sie_rcs(lib, solved):
     assert c1 == 0 and c2 == 0
     ref1, ref2 = op.rcs(x, d1), op.rcs(x, d2)
     assert np.all(ref1 > 0) and np.all(ref2 > 0)
-    assert np.abs(r1 - ref1).max() <= TOL * ref1.max()
-    assert np.abs(r2 - ref2).max() <= TOL * ref2.max()
+    assert np.abs(r1 - ref1).max() <= solved.tol * ref1.max()
+    assert np.abs(r2 - ref2).max() <= solved.tol * ref2.max()
     # and once more through the binding, back to the first set
     r3 = op.rcs_static(x, d1)
-    assert np.abs(r3 - ref1).max() <= TOL * ref1.max()
+    assert np.abs(r3 - ref1).max() <= solved.tol * ref1.max()
 
 
 def test_maximum_direction_count(lib, solved):
@@ -83,7 +89,7 @@ def test_maximum_direction_count(lib, solved):
     d = _dirs(n, 3)
     r = op.rcs_static(x, d)
     ref = op.rcs(x, d)
-    assert np.abs(r - ref).max() <= TOL * ref.max()
+    assert np.abs(r - ref).max() <= solved.tol * ref.max()
 
 
 def test_too_many_directions_is_an_error(lib, solved):
@@ -94,7 +100,7 @@ def test_too_many_directions_is_an_error(lib, solved):
     assert "SIE_RCS_STATIC_MAX_DIR" in lib.lib().sie_last_error().decode()
     # the array is untouched by the refused call: the next call is still exact
     d1 = _dirs(5, 5)
-    assert np.abs(op.rcs_static(x, d1) - op.rcs(x, d1)).max() <= TOL * op.rcs(x, d1).max()
+    assert np.abs(op.rcs_static(x, d1) - op.rcs(x, d1)).max() <= solved.tol * op.rcs(x, d1).max()
 
 
 def test_profiling_on_is_refused(lib, ctx, solved):
