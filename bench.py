@@ -214,7 +214,12 @@ FFT_GRIDS = {"fft_fwd_x": 7, "fft_fwd_y": 7, "fft_fwd_z": 7, "fft_inv_z": 4, "ff
 # DRAM bytes (read + write) per launch of a stage's kernels from one ncu capture
 # (profiles/), keyed by stage and path, with the hash of the library sources
 # the capture was taken at: a stale entry (kernels changed since) reads as null.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of a stage's kernel from one ncu capture,
+# with the hash of the library sources it was taken on (stale once they change).
+# k_fft_z_sys<7,2,double2> on the 128^3 FFT grid: the grid part has the same
+# size at every mesh level of the copper workload, so the capture on the
+# 480-RWG mesh holds per launch for the 30,720-RWG one.
+TRAFFIC = {("fft_z_specmul", "fp64"): (249870080 + 47390208, "f124e1ac95d297f3")}
 
 
 def source_hash():
