@@ -9,18 +9,17 @@ routine for S parameters (CPU).
   from the far field (Poynting), and Y = Y^T (reciprocity; L0 is complex
   symmetric), both to quadrature accuracy.  (A sign slip in the port vector,
   the excitation or the current extraction breaks the first pin.)
-* The radiated and absorbed powers themselves: plane-wave scattering by a
-  lossy sphere, scattered and absorbed power against the Mie series'
-  scattering and absorption cross sections.
+* The radiated and absorbed powers themselves are pinned against the Mie
+  cross sections of a lossy sphere in tests/test_system_oracle.py.
 * S from Y: the textbook series-impedance two-port and one-port loads; the
   library's sie_port_sparams (host code) against it.
 """
 import numpy as np
 import pytest
 
-from oracle import mie, mom, ports, system
+from oracle import mom, ports, system
 from oracle.rwg import Mesh
-from synth import box, cn_vector, icosphere
+from synth import box, cn_vector
 
 BAR = ((0.1, 0.01, 0.01), (10, 2, 2))   # 10 cm bar, 1 cm x 1 cm section, 176 triangles
 P2 = [((-0.02, 0.0, 0.0), (1.0, 0.0, 0.0), 0.02), ((0.02, 0.0, 0.0), (1.0, 0.0, 0.0), 0.02)]
@@ -105,29 +104,6 @@ def test_pec_reciprocity(bar, pec, f):
     assert abs(Y[0, 1] - Y[1, 0]) <= 1e-6 * abs(Y[0, 1])
     # the two ports sit symmetrically on the bar
     assert abs(Y[0, 0] - Y[1, 1]) <= 1e-6 * abs(Y[0, 0])
-
-
-def test_powers_match_mie_cross_sections():
-    """Lossy sphere (r = 1 mm, sigma = 1e4 S/m, 10 GHz, near-only interior),
-    plane wave of 1 V/m: scattered power = C_sca / (2 eta0), absorbed power
-    (into the object through its surface) = (C_ext - C_sca) / (2 eta0), with
-    the cross sections from the Mie coefficients."""
-    V, T = icosphere(2, 1e-3, equal_volume=True)
-    m = Mesh(V, T)
-    f, sig = 10e9, 1e4
-    ki = system.k_medium(f, 1.0, sig)
-    S = system.DenseGIBC(m, f, 1.0, sig, interior="near", cutoff=5.0 / abs(ki.imag))
-    H, E = S.solve(system.rhs_planewave(m, S.k0, [0, 0, -1], [1, 0, 0]))
-    a, b = mie.coefficients(S.k0 * 1e-3, mie.rel_index(1.0, sig, f))
-    n = np.arange(1, len(a) + 1)
-    c_ext = 2 * np.pi / S.k0 ** 2 * np.sum((2 * n + 1) * (a + b).real)
-    c_sca = 2 * np.pi / S.k0 ** 2 * np.sum((2 * n + 1) * (abs(a) ** 2 + abs(b) ** 2))
-    i0 = 1.0 / (2 * system.ETA0)
-    p_sca = ports.radiated_power(m, S.k0, H, E)
-    p_abs = ports.object_power(S.Ix, H, E)
-    print("P_sca", p_sca, c_sca * i0, "P_abs", p_abs, (c_ext - c_sca) * i0)
-    assert abs(p_sca / (c_sca * i0) - 1) <= 1e-3
-    assert abs(p_abs / ((c_ext - c_sca) * i0) - 1) <= 2e-3
 
 
 def test_sparams_closed_forms():

@@ -64,19 +64,45 @@ def test_pec_limit_rcs(diel2):
     assert abs(got / mie.backscatter_rcs(0.01, 3e9, pec=True) - 1) < 0.01
 
 
-def test_lossy_near_only_interior_rcs():
-    """Conductive sphere (sigma = 1e4 S/m, 10 GHz, r = 1 mm, skin depth 50 um):
-    interior operators restricted to the 5-skin-depth cutoff (Sec. V) and
-    solved as a sparse near-only Z_i; RCS within 1% of Mie."""
+@pytest.fixture(scope="module")
+def lossy2():
+    """Conductive sphere (sigma = 1e4 S/m, 10 GHz, r = 1 mm, skin depth 50 um,
+    320 triangles), interior operators restricted to the 5-skin-depth cutoff
+    (Sec. V), solved for the x-polarised plane wave along -z."""
     V, T = icosphere(2, 1e-3, equal_volume=True)
     m = Mesh(V, T)
     ki = system.k_medium(10e9, 1.0, 1e4)
     S = system.DenseGIBC(m, 10e9, 1.0, 1e4, interior="near", cutoff=5.0 / abs(ki.imag))
-    b = system.rhs_planewave(m, S.k0, [0, 0, -1], [1, 0, 0])
-    H, E = S.solve(b)
+    H, E = S.solve(system.rhs_planewave(m, S.k0, [0, 0, -1], [1, 0, 0]))
+    return m, S, H, E
+
+
+def test_lossy_near_only_interior_rcs(lossy2):
+    """Near-only Z_i as a sparse solve: RCS within 1% of Mie."""
+    m, S, H, E = lossy2
     got = system.rcs(m, S.k0, H, E, [[0, 0, 1]])[0]
     ref = mie.backscatter_rcs(1e-3, 10e9, 1.0, 1e4)
     assert abs(got / ref - 1) < 0.01
+
+
+def test_powers_match_mie_cross_sections(lossy2):
+    """The radiated and absorbed powers of oracle/ports.py (the pins of the
+    port model): plane wave of 1 V/m on the lossy sphere, scattered power =
+    C_sca / (2 eta0), power into the object through its surface =
+    (C_ext - C_sca) / (2 eta0), the cross sections from the Mie
+    coefficients."""
+    from oracle import ports
+    m, S, H, E = lossy2
+    a, b = mie.coefficients(S.k0 * 1e-3, mie.rel_index(1.0, 1e4, 10e9))
+    n = np.arange(1, len(a) + 1)
+    c_ext = 2 * np.pi / S.k0 ** 2 * np.sum((2 * n + 1) * (a + b).real)
+    c_sca = 2 * np.pi / S.k0 ** 2 * np.sum((2 * n + 1) * (abs(a) ** 2 + abs(b) ** 2))
+    i0 = 1.0 / (2 * system.ETA0)
+    p_sca = ports.radiated_power(m, S.k0, H, E)
+    p_abs = ports.object_power(S.Ix, H, E)
+    print("P_sca", p_sca, c_sca * i0, "P_abs", p_abs, (c_ext - c_sca) * i0)
+    assert abs(p_sca / (c_sca * i0) - 1) <= 1e-3
+    assert abs(p_abs / ((c_ext - c_sca) * i0) - 1) <= 2e-3
 
 
 @pytest.fixture(scope="module")
