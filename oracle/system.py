@@ -229,6 +229,19 @@ class AimGIBC:
             self._lu_dense = sla.lu_factor(Li)
             self._Ki = Ki
 
+    def with_sibc(self):
+        """The same system with the surface impedance condition as its
+        interior (the exterior operators shared, not rebuilt)."""
+        import copy
+        import scipy.sparse as sp
+        import scipy.sparse.linalg as spl
+        other = copy.copy(self)
+        for name in ("_lu", "_lu_dense", "_Ki", "inn"):
+            other.__dict__.pop(name, None)
+        other._sibc = eta_medium(self.f, self.eps_r, self.sigma) / ETA0
+        other._lu_gram = spl.splu(sp.csc_matrix(mom.gram(self.mesh).astype(complex)))
+        return other
+
     def Z(self, H):
         if hasattr(self, "_sibc"):
             return self._sibc * self._lu_gram.solve(self.Ix @ H)

@@ -56,16 +56,12 @@ def oracle_admittances(m):
     * G[i] = W^-1 A1^-T [p_i; 0] with W = diag(1, q_w) (q_w = mean |L_A,mm|,
       the weight of the library's residual norm): the error of port current
       i after a solve with weighted residual r is |G[i] . (W r)|."""
-    import copy
     import scipy.linalg as sla
-    import scipy.sparse as sp
     import scipy.sparse.linalg as spl
     from oracle import mom
     g = aim.grid_params(m, M=2)
     s_near = system.AimGIBC(m, F, 1.0, SIGMA, g, interior="near", cutoff=_cutoff())
-    s_sibc = copy.copy(s_near)
-    s_sibc._sibc = system.eta_medium(F, 1.0, SIGMA) / system.ETA0
-    s_sibc._lu_gram = spl.splu(sp.csc_matrix(mom.gram(m).astype(complex)))
+    s_sibc = s_near.with_sibc()
     d = system.DenseGIBC(m, F, 1.0, SIGMA, interior="near", cutoff=_cutoff())
     z_sibc = system.z_sibc(m, F, 1.0, SIGMA, mom.gram(m), d.Ix)
     Dm = system.incidence_sparse(m)

@@ -200,6 +200,20 @@ def test_sibc_is_the_gibc_limit():
     assert d < 3e-3, d
 
 
+def test_aim_system_with_sibc_interior(aimsys):
+    """AimGIBC.with_sibc(): the same exterior, Z' = (eta_i / eta0) G^-1 Ix as
+    in the dense SIBC form (the near-only system it was made from is left
+    unchanged)."""
+    m, S, D = aimsys
+    H = cn_vector(m.ne, 51)
+    z_near = S.Z(H)
+    sb = S.with_sibc()
+    ref = system.z_sibc(m, 10e9, 1.0, 1e4, mom.gram(m), mom.Ix(m)) @ H
+    assert sb.ext is S.ext
+    assert np.linalg.norm(sb.Z(H) - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert np.array_equal(S.Z(H), z_near)
+
+
 def test_objects_oracle_one_object_is_aim_system():
     """The several-object oracle with one object reduces to the one-object AIM
     system (its per-object restriction and block assembly pinned)."""
