@@ -113,6 +113,25 @@ def sparams(Y, z_ref=50.0):
     return (E - z_ref * Y) @ np.linalg.inv(E + z_ref * Y)
 
 
+def thevenin_sparams(mesh, ports_, A, z_ref=50.0):
+    """S of the ports from Thevenin sources: every port loaded by z_ref, port
+    j driven by a 1 V source in series with it.  The port voltage V = e -
+    z_ref I enters the right-hand side, and with I = -p . H the load moves
+    to the matrix: (A + (z_ref/eta0) P^T P) H = -(e_j/eta0) p_j (first
+    block of Eq. sys, A: the ne x ne system with the charge unknowns
+    eliminated).  Incident and reflected waves a = (V + z I) / (2 sqrt z),
+    b = (V - z I) / (2 sqrt z) give S_ij = delta_ij - 2 z I_i."""
+    P = np.array([port_vector(mesh, pt) for pt in ports_])
+    Az = A + (z_ref / ETA0) * (P.T @ P)
+    n = len(ports_)
+    S = np.zeros((n, n), complex)
+    for j in range(n):
+        H = np.linalg.solve(Az, -P[j] / ETA0)
+        I = -(P @ H)
+        S[:, j] = np.eye(n)[:, j] - 2 * z_ref * I
+    return S
+
+
 def sphere_rule(nth, nph):
     """Directions and weights integrating over the unit sphere: Gauss-Legendre
     in cos(theta), the trapezoidal rule in phi (exact on spherical harmonics

@@ -11,8 +11,9 @@ routine for S parameters (CPU).
   the excitation or the current extraction breaks the first pin.)
 * The radiated and absorbed powers themselves are pinned against the Mie
   cross sections of a lossy sphere in tests/test_system_oracle.py.
-* S from Y: the textbook series-impedance two-port and one-port loads; the
-  library's sie_port_sparams (host code) against it.
+* S from Y: the textbook series-impedance two-port and one-port loads; S
+  measured directly with Thevenin sources and loads inside the field solve;
+  the library's sie_port_sparams (host code) against it.
 """
 import numpy as np
 import pytest
@@ -104,6 +105,19 @@ def test_pec_reciprocity(bar, pec, f):
     assert abs(Y[0, 1] - Y[1, 0]) <= 1e-6 * abs(Y[0, 1])
     # the two ports sit symmetrically on the bar
     assert abs(Y[0, 0] - Y[1, 1]) <= 1e-6 * abs(Y[0, 0])
+
+
+@pytest.mark.parametrize("f", [0.3e9, 1.5e9])
+def test_sparams_equal_thevenin_excitation(bar, pec, f):
+    """S from Y (ports shorted, one driven) equals S measured directly with a
+    Thevenin source and load of z_ref on every port (the loads inside the
+    field solve), the excitation the paper uses (Sec. V)."""
+    k0, A = pec[f]
+    Y = ports.admittance(bar, P2, lambda b: np.linalg.solve(A, b))
+    S_th = ports.thevenin_sparams(bar, P2, A, 50.0)
+    S_y = ports.sparams(Y, 50.0)
+    print(f, "S", S_y, "thevenin vs Y", np.abs(S_th - S_y).max())
+    assert np.abs(S_th - S_y).max() <= 1e-9
 
 
 def test_sparams_closed_forms():
