@@ -376,27 +376,31 @@ typedef struct {
     double radius;      /* only edges within this distance of origin (m)         */
 } sie_port;
 
-/* The edges of one port (ascending edge numbers) and their signs s_m.  Call
+/* The edges of one port (the port loop of Sec. II's port excitation, in the
+ * delta-gap model above; ascending edge numbers) and their signs s_m.  Call
  * with edge or sign NULL to get the count in *n; then with buffers of *n
  * entries (host).  SIE_ERR_ARG when no edge qualifies, an edge in the plane
  * does not separate its triangles, or the port's numbers are not finite. */
 sie_status sie_port_edges(const sie_mesh* mesh, const sie_port* port, int32_t* edge, int32_t* sign, int64_t* n);
 
-/* Right-hand sides of the ports: nport vectors of N_e + N_t complex128
+/* Right-hand sides of the ports (the port excitation of Sec. II entering
+ * Eq. (EFIE01dis) like E_inc): nport vectors of N_e + N_t complex128
  * ([first block; zero charge rows], the layout of sie_solve), vector j with
  * port j driven by volts[j] volts (volts NULL: 1 V) and the other ports
  * shorted.  flags: SIE_DEVICE_PTRS for a device b.  Allocates and frees
  * small device buffers; synchronises. */
 sie_status sie_rhs_ports(sie_op* op, const sie_port* ports, int nport, const double* volts, double* b, int flags);
 
-/* Port currents I = -p_i . H_r of nrhs solutions x (N_e + N_t complex128
+/* Port currents (Sec. V: the port quantities the S parameters come from)
+ * I = -p_i . H_r of nrhs solutions x (N_e + N_t complex128
  * each, as sie_solve returns them): I[r * nport + i] (complex128, host).
  * flags: SIE_DEVICE_PTRS for a device x.  Allocates and frees small device
  * buffers; synchronises. */
 sie_status sie_port_currents(sie_op* op, const sie_port* ports, int nport, const double* x, int nrhs, double* I,
                              int flags);
 
-/* Admittance matrix of the ports: one solve per port (sie_solve with nport
+/* Admittance matrix of the ports (Sec. V network parameters): one solve per
+ * port (sie_solve with nport
  * right-hand sides, lockstep blocks of 8), then the port currents.
  * Y: nport x nport complex128 row-major on the host, Y[i * nport + j] =
  * current through port i per volt on port j.  iters, relres: per port (host
@@ -407,7 +411,8 @@ sie_status sie_port_currents(sie_op* op, const sie_port* ports, int nport, const
 sie_status sie_port_admittance(sie_op* op, const sie_port* ports, int nport, double* Y, int* iters, double* relres,
                                int flags);
 
-/* S parameters from an admittance matrix for one real reference impedance
+/* S parameters (Sec. V, Figs. of the package and interconnect examples)
+ * from an admittance matrix for one real reference impedance
  * z_ref (ohm) on every port: S = (1 - z_ref Y)(1 + z_ref Y)^-1.  Y, S:
  * nport x nport complex128 row-major, host.  Host arithmetic only (Gaussian
  * elimination with partial pivoting).  SIE_ERR_ARG when 1 + z_ref Y is
