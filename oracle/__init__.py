@@ -17,6 +17,12 @@ dielectric and lossy objects of arbitrary conductivity", that it follows):
                 (direct sum and FFT), near-region correction (Eqs. LinNRP/KinNRP).
 * ``bounds`` -- the Lagrange interpolation error bound of Eqs. (Lbounds)-(Ddef).
 * ``mie``    -- Mie series of a homogeneous sphere (the paper's RCS check).
+* ``system`` -- the dense and AIM forms of Eqs. (GIBCsys) and (sys),
+                plane-wave excitation, RCS, SIBC, several objects.
+* ``ports``  -- delta-gap ports, admittance and S parameters (Secs. II, V),
+                radiated and absorbed power.
+* ``dual``   -- dual (Buffa-Christiansen) basis on the barycentric
+                refinement (Sec. V discussion).
 
 Parity status of each function is stated in its docstring; a function with
 no independent pin says "parity unpinned".
